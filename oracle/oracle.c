@@ -1,0 +1,336 @@
+/*
+ * Swept-rule oracle: plain, slow, per-step CPU stepping of a 1D periodic
+ * explicit scheme.
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library.  It shares no code, header, table
+ * or constant generator with the CUDA path.
+ *
+ * What it computes.  The swept rule (Sections 2-3) is an exact reordering of
+ * per-step time stepping: every sub-timestep output is computed once, from
+ * the same inputs, with no redundant or approximate work (Abstract;
+ * Section 1, comparison with communication-avoiding methods).  So the oracle
+ * is the definition itself: apply the sub-timestep to every point of the
+ * periodic grid, one time level after another (Section 2; Section 3 fixes the
+ * periodic 1D domain).
+ *
+ * Sub-timestep expressions.  The paper gives the schemes in words (Section 2:
+ * a finite-difference sub-timestep that reads a point and its two
+ * neighbours; Section 6: finite differences for Kuramoto-Sivashinsky) but no
+ * evaluation order.  This file fixes one; it is the canonical order for the
+ * whole project (the GPU kernels restate it independently):
+ *
+ *   heat  u_t = u_xx,  r = dt/dx^2 (Table 2 counts 3 FLOP per point):
+ *       s  = u[i-1] + u[i+1]
+ *       w  = s - 2*u[i]                      (2*u exact, one rounding)
+ *       u' = fma(r, w, u[i])
+ *
+ *   Kuramoto-Sivashinsky  u_t = -u u_x - u_xx - u_xxxx  (Section 6), central
+ *   differences, flux u^2/2, the 3-point second difference applied twice:
+ *       G[j] = u[j]*u[j]
+ *       w[j] = (u[j-1] + u[j+1]) - 2*u[j]
+ *       D    = (w[i-1] + w[i+1]) - 2*w[i]
+ *       t    = G[i+1] - G[i-1]
+ *       u'   = fma(e, D, fma(b, w[i], fma(a, t, u[i])))
+ *     with a = -(dt/(4 dx)), b = -(dt/(dx dx)), e = -(dt/((dx dx)(dx dx))),
+ *     computed here in FP64 in exactly that order.
+ *
+ *   FP32-compensated state (hi, lo), value = hi + lo:
+ *       the stencil terms above are evaluated in FP32 on hi only,
+ *       heat: y = fmaf(r, w, lo)
+ *       KS:   y = fmaf(e, D, fmaf(b, w, fmaf(a, t, lo)))
+ *       (hi', lo') = TwoSum(hi, y)           (Knuth, 6 operations)
+ *     FP32 constants are the FP64 constants rounded to nearest.
+ *     Split: hi = (float)u, lo = (float)(u - (double)hi);
+ *     merge: u = (double)hi + (double)lo.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off (no fast-math).  fma()/fmaf()
+ * are the C library's correctly rounded fused multiply-adds.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { OR_HEAT = 0, OR_KS = 1 };
+enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2 };
+
+typedef struct {
+    int stencil;
+    int radius;
+    double r;            /* heat */
+    double a, b, e;      /* KS */
+    float r32, a32, b32, e32;
+} or_consts;
+
+static int make_consts(int stencil, const double *prm, or_consts *c)
+{
+    memset(c, 0, sizeof *c);
+    c->stencil = stencil;
+    if (stencil == OR_HEAT) {
+        c->radius = 1;
+        c->r = prm[0];
+        c->r32 = (float)c->r;
+        return OR_OK;
+    }
+    if (stencil == OR_KS) {
+        double dt = prm[0], dx = prm[1];
+        if (!(dx > 0.0)) return OR_EINVAL;
+        double dx2 = dx * dx;
+        c->radius = 2;
+        c->a = -(dt / (4.0 * dx));
+        c->b = -(dt / dx2);
+        c->e = -(dt / (dx2 * dx2));
+        c->a32 = (float)c->a;
+        c->b32 = (float)c->b;
+        c->e32 = (float)c->e;
+        return OR_OK;
+    }
+    return OR_EINVAL;
+}
+
+static inline int64_t wrap(int64_t i, int64_t n)
+{
+    if (i >= 0 && i < n) return i;
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+/* ---------------------------------------------------------------- FP64 -- */
+
+/* One sub-timestep at point i, reading u[i-2..i+2] (periodic). */
+static inline double point_f64(const or_consts *c, const double *u, int64_t i, int64_t n)
+{
+    if (c->stencil == OR_HEAT) {
+        double um = u[wrap(i - 1, n)], u0 = u[i], up = u[wrap(i + 1, n)];
+        double s = um + up;
+        double w = s - 2.0 * u0;
+        return fma(c->r, w, u0);
+    } else {
+        double v[5];
+        for (int k = -2; k <= 2; ++k) v[k + 2] = u[wrap(i + k, n)];
+        double Gm = v[1] * v[1];
+        double Gp = v[3] * v[3];
+        double wm = (v[0] + v[2]) - 2.0 * v[1];
+        double w0 = (v[1] + v[3]) - 2.0 * v[2];
+        double wp = (v[2] + v[4]) - 2.0 * v[3];
+        double D = (wm + wp) - 2.0 * w0;
+        double t = Gp - Gm;
+        return fma(c->e, D, fma(c->b, w0, fma(c->a, t, v[2])));
+    }
+}
+
+int oracle_step_f64(int stencil, const double *prm, const double *u, double *out, int64_t n)
+{
+    or_consts c;
+    if (n <= 0 || make_consts(stencil, prm, &c) != OR_OK) return OR_EINVAL;
+    for (int64_t i = 0; i < n; ++i) out[i] = point_f64(&c, u, i, n);
+    return OR_OK;
+}
+
+/* u <- u after nsteps sub-timesteps (in place).  nthreads <= 0: default. */
+int oracle_advance_f64(int stencil, const double *prm, double *u, int64_t n,
+                       int64_t nsteps, int nthreads)
+{
+    or_consts c;
+    if (n <= 0 || nsteps < 0 || make_consts(stencil, prm, &c) != OR_OK) return OR_EINVAL;
+    if (nsteps == 0) return OR_OK;
+    double *tmp = (double *)malloc((size_t)n * sizeof(double));
+    if (!tmp) return OR_ENOMEM;
+    double *src = u, *dst = tmp;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) dst[i] = point_f64(&c, src, i, n);
+        double *t = src; src = dst; dst = t;
+    }
+    if (src != u) memcpy(u, src, (size_t)n * sizeof(double));
+    free(tmp);
+    return OR_OK;
+}
+
+/* ------------------------------------------------- FP32 compensated ---- */
+
+static inline void two_sum(float a, float b, float *s, float *err)
+{
+    float x = a + b;
+    float bb = x - a;
+    float ea = a - (x - bb);
+    float eb = b - bb;
+    *s = x;
+    *err = ea + eb;
+}
+
+static inline void point_f32c(const or_consts *c, const float *hi, const float *lo,
+                              int64_t i, int64_t n, float *ho, float *lout)
+{
+    float y;
+    float h0 = hi[i];
+    if (c->stencil == OR_HEAT) {
+        float hm = hi[wrap(i - 1, n)], hp = hi[wrap(i + 1, n)];
+        float s = hm + hp;
+        float w = s - 2.0f * h0;
+        y = fmaf(c->r32, w, lo[i]);
+    } else {
+        float v[5];
+        for (int k = -2; k <= 2; ++k) v[k + 2] = hi[wrap(i + k, n)];
+        float Gm = v[1] * v[1];
+        float Gp = v[3] * v[3];
+        float wm = (v[0] + v[2]) - 2.0f * v[1];
+        float w0 = (v[1] + v[3]) - 2.0f * v[2];
+        float wp = (v[2] + v[4]) - 2.0f * v[3];
+        float D = (wm + wp) - 2.0f * w0;
+        float t = Gp - Gm;
+        y = fmaf(c->e32, D, fmaf(c->b32, w0, fmaf(c->a32, t, lo[i])));
+    }
+    two_sum(h0, y, ho, lout);
+}
+
+int oracle_split_f32c(const double *u, float *hi, float *lo, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float h = (float)u[i];
+        hi[i] = h;
+        lo[i] = (float)(u[i] - (double)h);
+    }
+    return OR_OK;
+}
+
+int oracle_merge_f32c(const float *hi, const float *lo, double *u, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) u[i] = (double)hi[i] + (double)lo[i];
+    return OR_OK;
+}
+
+int oracle_step_f32c(int stencil, const double *prm, const float *hi, const float *lo,
+                     float *hi_out, float *lo_out, int64_t n)
+{
+    or_consts c;
+    if (n <= 0 || make_consts(stencil, prm, &c) != OR_OK) return OR_EINVAL;
+    for (int64_t i = 0; i < n; ++i) point_f32c(&c, hi, lo, i, n, &hi_out[i], &lo_out[i]);
+    return OR_OK;
+}
+
+int oracle_advance_f32c(int stencil, const double *prm, float *hi, float *lo, int64_t n,
+                        int64_t nsteps, int nthreads)
+{
+    or_consts c;
+    if (n <= 0 || nsteps < 0 || make_consts(stencil, prm, &c) != OR_OK) return OR_EINVAL;
+    if (nsteps == 0) return OR_OK;
+    float *th = (float *)malloc((size_t)n * sizeof(float));
+    float *tl = (float *)malloc((size_t)n * sizeof(float));
+    if (!th || !tl) { free(th); free(tl); return OR_ENOMEM; }
+    float *sh = hi, *sl = lo, *dh = th, *dl = tl;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) point_f32c(&c, sh, sl, i, n, &dh[i], &dl[i]);
+        float *t;
+        t = sh; sh = dh; dh = t;
+        t = sl; sl = dl; dl = t;
+    }
+    if (sh != hi) {
+        memcpy(hi, sh, (size_t)n * sizeof(float));
+        memcpy(lo, sl, (size_t)n * sizeof(float));
+    }
+    free(th);
+    free(tl);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------- adjoint ------ */
+
+/*
+ * Discrete adjoint of the FP64 stepper (reverse-mode derivative of the
+ * composed map u0 -> u(nsteps)).  With Phi the one-step map, the cotangent
+ * runs backwards as lambda^n = (dPhi/du (u^n))^T lambda^{n+1}; grad = lambda^0.
+ *
+ * The Jacobian of the canonical expressions in exact arithmetic:
+ *   heat: dPhi = I + r*L2, L2 the periodic 3-point second difference, which
+ *         is symmetric, so lambda' = lambda + r*L2 lambda.
+ *   KS:   dPhi = I + a*dT + b*L2 + e*L2*L2 with (dT v)_i = 2 u_{i+1} v_{i+1}
+ *         - 2 u_{i-1} v_{i-1}; its transpose is (dT^T l)_j = 2 u_j (l_{j-1}
+ *         - l_{j+1}); L2 and L2*L2 are symmetric.
+ *
+ * Written as a plain dense-in-time computation: the whole trajectory is
+ * stored (n * nsteps doubles), so it is for small cases only.
+ *
+ * Evaluation order (canonical for the adjoint):
+ *   heat: w = (l[j-1] + l[j+1]) - 2 l[j];  l' = fma(r, w, l[j])
+ *   KS:   W[j] = (l[j-1] + l[j+1]) - 2 l[j];  D = (W[j-1] + W[j+1]) - 2 W[j];
+ *         q = l[j-1] - l[j+1];  c = (2a) * u[j];
+ *         l' = fma(e, D, fma(b, W[j], fma(c, q, l[j])))
+ */
+static void adjoint_point_pass(const or_consts *c, const double *u, const double *l,
+                               double *out, int64_t n)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        if (c->stencil == OR_HEAT) {
+            double s = l[wrap(j - 1, n)] + l[wrap(j + 1, n)];
+            double w = s - 2.0 * l[j];
+            out[j] = fma(c->r, w, l[j]);
+        } else {
+            double v[5];
+            for (int k = -2; k <= 2; ++k) v[k + 2] = l[wrap(j + k, n)];
+            double Wm = (v[0] + v[2]) - 2.0 * v[1];
+            double W0 = (v[1] + v[3]) - 2.0 * v[2];
+            double Wp = (v[2] + v[4]) - 2.0 * v[3];
+            double D = (Wm + Wp) - 2.0 * W0;
+            double q = v[1] - v[3];
+            double cj = (2.0 * c->a) * u[j];
+            out[j] = fma(c->e, D, fma(c->b, W0, fma(cj, q, v[2])));
+        }
+    }
+}
+
+int oracle_adjoint_f64(int stencil, const double *prm, const double *u0, const double *lam_T,
+                       double *grad, int64_t n, int64_t nsteps)
+{
+    or_consts c;
+    if (n <= 0 || nsteps < 0 || make_consts(stencil, prm, &c) != OR_OK) return OR_EINVAL;
+    double *traj = (double *)malloc((size_t)n * (size_t)(nsteps + 1) * sizeof(double));
+    double *tmp = (double *)malloc((size_t)n * sizeof(double));
+    if (!traj || !tmp) { free(traj); free(tmp); return OR_ENOMEM; }
+    memcpy(traj, u0, (size_t)n * sizeof(double));
+    for (int64_t s = 0; s < nsteps; ++s)
+        for (int64_t i = 0; i < n; ++i)
+            traj[(s + 1) * n + i] = point_f64(&c, traj + s * n, i, n);
+    memcpy(grad, lam_T, (size_t)n * sizeof(double));
+    for (int64_t s = nsteps - 1; s >= 0; --s) {
+        adjoint_point_pass(&c, traj + s * n, grad, tmp, n);
+        memcpy(grad, tmp, (size_t)n * sizeof(double));
+    }
+    free(traj);
+    free(tmp);
+    return OR_OK;
+}
+
+/* One adjoint step (transpose Jacobian at state u applied to l), for tests. */
+int oracle_adjoint_step_f64(int stencil, const double *prm, const double *u, const double *l,
+                            double *out, int64_t n)
+{
+    or_consts c;
+    if (n <= 0 || make_consts(stencil, prm, &c) != OR_OK) return OR_EINVAL;
+    adjoint_point_pass(&c, u, l, out, n);
+    return OR_OK;
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
