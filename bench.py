@@ -1,0 +1,359 @@
+"""Benchmark of the swept-rule hot path on one GB300 (or N independent replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload: 1D heat, periodic, N = 2^24 points, r = 1/4, 20000 sub-timesteps
+per step, compensated FP32 state, tile B = 512; u0 = uniform[-1,1] noise
+plus 16 low modes.  One "step" is one swept_advance of the whole field
+through all 20000 sub-timesteps (q + 2 = 80 stage launches).
+
+Metric: cell-updates/s = N * nsteps / time.  Every step starts from the same
+device-resident input (restored outside the timed events); L2 is flushed
+between steps (a 256 MiB write), also outside the timed events.
+
+Printed as one JSON line: the device-timed value, the end-to-end value
+through the public API with host buffers, the roofline of the dominant
+kernel, the CPU oracle baseline and the SM clocks seen during the run.
+Also measured (outside the timed region, one step each): the naive per-step
+stepper and the FP64 state, and the compensated result's max error against
+the exact Fourier solution.
+
+--impl reference times the CPU oracle (the plain per-step definition, in
+C with OpenMP on the host cores) on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank runs its own replica (the single-problem
+path has no cross-GPU exchange); the max time over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+N_POINTS = 1 << 24
+NSTEPS = 20000
+TILE_B = 512
+HEAT_R = 0.25
+METRIC = "cell-updates/s (N x steps / s), swept vs naive stepper, 1 GB300, at stated error"
+UNIT = "cell-updates/s"
+OPS_PER_UPDATE_F32C_HEAT = 9     # s, w, y, TwoSum (6): FP32 add/sub/mul/fma instructions
+OPS_PER_UPDATE_F64_HEAT = 3
+
+
+def workload_config(n_gpus: int):
+    return {"workload": "heat1d_periodic_N16777216_r0.25_20000steps_f32c_B512",
+            "N": N_POINTS, "nsteps": NSTEPS, "B": TILE_B, "stencil": "heat 3-point forward Euler",
+            "state": "f32 compensated (hi, lo)", "l2": "flushed between steps (256 MiB write)",
+            "input": "device-resident, restored between steps", "parallelism": f"replicas x{n_gpus}"}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU oracle
+def time_oracle(target_s: float = 12.0):
+    """The oracle (compensated FP32 per-step stepping, OpenMP) on a bounded sample."""
+    import oracle
+    u0 = workloads.heat_noise_modes(N_POINTS)
+    hi, lo = oracle.split_f32c(u0)
+    threads = cores_used()
+    t0 = time.perf_counter()
+    oracle.advance_f32c(oracle.HEAT, [HEAT_R], hi, lo, 2, threads)
+    dt = max(time.perf_counter() - t0, 1e-6) / 2
+    steps = max(2, min(NSTEPS, int(target_s / dt)))
+    t0 = time.perf_counter()
+    oracle.advance_f32c(oracle.HEAT, [HEAT_R], hi, lo, steps, threads)
+    el = time.perf_counter() - t0
+    return {"value": N_POINTS * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"N=2^24, first {steps} of 20000 sub-timesteps, {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    u0 = workloads.heat_noise_modes(N_POINTS)
+    hi0, lo0 = oracle.split_f32c(u0)
+    threads = cores_used()
+    # size one step so that warmup + steps take about two minutes in total
+    t0 = time.perf_counter()
+    oracle.advance_f32c(oracle.HEAT, [HEAT_R], hi0, lo0, 2, threads)
+    per = max(time.perf_counter() - t0, 1e-6) / 2
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    sample_steps = max(1, min(NSTEPS, int(budget / per)))
+    for _ in range(args.warmup):
+        oracle.advance_f32c(oracle.HEAT, [HEAT_R], hi0, lo0, sample_steps, threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.advance_f32c(oracle.HEAT, [HEAT_R], hi0, lo0, sample_steps, threads)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = N_POINTS * sample_steps * args.steps / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
+            "impl": "reference", "config": workload_config(args.gpus),
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value, "unit": UNIT,
+                             "sample": f"N=2^24, {sample_steps} of 20000 sub-timesteps per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_1504_01380_gb300 as sw
+    sw.load()
+
+    u0 = workloads.heat_noise_modes(N_POINTS)
+    u0_dev = torch.tensor(u0, device=dev)
+    plan = sw.swept_plan(N_POINTS, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, TILE_B)
+    pristine = sw.swept_f32c_split(u0_dev)
+    u = torch.empty_like(pristine)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    h = plan.h
+    launches_per_step = NSTEPS // h + (2 if NSTEPS % h else 1)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def one(timed_list=None):
+        u.copy_(pristine)
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sw.swept_advance(plan, u, NSTEPS)
+        e1.record(stream)
+        if timed_list is not None:
+            timed_list.append((e0, e1))
+
+    for _ in range(args.warmup):
+        one()
+    barrier()
+    events = []
+    with ClockSampler(dev.index) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            one(events)
+        barrier()
+        wall = time.perf_counter() - wall0
+    ms = [a.elapsed_time(b) for a, b in events]
+    t_dev = sum(ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_dev], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    updates = N_POINTS * NSTEPS * args.steps * world
+    value = updates / t_dev
+    clocks = clk.summary()
+
+    # ---- end to end through the public API: pinned host in, pinned host out
+    host_in = torch.tensor(u0).pin_memory()
+    host_out = torch.empty(N_POINTS, dtype=torch.float64).pin_memory()
+    dev64 = torch.empty(N_POINTS, dtype=torch.float64, device=dev)
+
+    def e2e_step():
+        dev64.copy_(host_in, non_blocking=True)
+        sw.swept_f32c_split(dev64, out=u)
+        sw.swept_advance(plan, u, NSTEPS)
+        sw.swept_f32c_merge(u, out=dev64)
+        host_out.copy_(dev64, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_times.append(a.elapsed_time(b) / 1e3)
+    e2e_value = N_POINTS * NSTEPS * world / statistics.mean(e2e_times)
+
+    # stated error: compensated result against the exact Fourier solution
+    got = host_out.numpy()
+    k = np.arange(N_POINTS // 2 + 1)
+    exact = np.fft.irfft(np.fft.rfft(u0) * (1.0 - np.sin(np.pi * k / N_POINTS) ** 2) ** NSTEPS,
+                         N_POINTS)
+    max_err = float(np.max(np.abs(got - exact)) / np.max(np.abs(u0)))
+
+    # ---- comparison runs (one step each, outside the timed region)
+    def timed(fn):
+        u.copy_(pristine)
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    naive_f32c = N_POINTS * NSTEPS / timed(lambda: sw.swept_naive_advance(plan, u, NSTEPS))
+    plan64 = sw.swept_plan(N_POINTS, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, TILE_B)
+    u64 = u0_dev.clone()
+
+    def timed64(fn):
+        u64.copy_(u0_dev)
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    swept_f64 = N_POINTS * NSTEPS / timed64(lambda: sw.swept_advance(plan64, u64, NSTEPS))
+    naive_f64 = N_POINTS * NSTEPS / timed64(lambda: sw.swept_naive_advance(plan64, u64, NSTEPS))
+    plan64.destroy()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # dominant kernel: the swept stage kernel (heat, compensated FP32, K = 16)
+    per_launch_ops = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * h
+    avg_launch_s = (t_dev / world / args.steps) / launches_per_step
+    peak_ops = 152 * 128 * sm_max * 1e6
+    achieved = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * NSTEPS / (t_dev / world / args.steps)
+    roof = {"bound": "alu", "kernel": "swept_stage_kernel<heat,f32c,K=16>",
+            "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak_ops, "traffic": None,
+            "per_launch_ops": per_launch_ops, "avg_launch_ms": avg_launch_s * 1e3,
+            "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"}
+    cpu = time_oracle() if world == 1 else None
+    naive_roof = hbm * 1e9 / 16.0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / world / args.steps * world / world,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32c",
+            "data": "synthetic", "config": workload_config(world),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N_POINTS,
+                    "d2h_bytes_per_step": 8 * N_POINTS},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "max_err_vs_exact": max_err,
+            "compare": {"naive_f32c": naive_f32c, "swept_f64": swept_f64, "naive_f64": naive_f64,
+                        "naive_hbm_roof_16B": naive_roof, "swept_over_naive_hbm_roof": value / world / naive_roof,
+                        "ops_per_update": {"f32c_heat": OPS_PER_UPDATE_F32C_HEAT, "f64_heat": OPS_PER_UPDATE_F64_HEAT}},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

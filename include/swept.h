@@ -1,0 +1,159 @@
+/*
+ * swept.h -- C ABI of the swept-rule library for one NVIDIA GB300 (sm_103a).
+ *
+ * The library advances a 1D periodic field u by nsteps explicit sub-timesteps
+ * of a local stencil.  The swept rule (Sections 3-4 of Alhubail & Wang,
+ * "The swept rule for breaking the latency barrier in time advancing PDEs")
+ * tiles space-time into shrinking triangles and diamonds so that each tile of
+ * B points advances B/(2r) sub-timesteps on chip between exchanges of its
+ * leading edges.  The result equals per-step stepping exactly.
+ *
+ * Conventions for every entry point
+ *   - Return value: SWEPT_OK (0) or a negative SWEPT_E* code; nothing is
+ *     thrown or aborted across the ABI.  swept_strerror() names a code.
+ *   - Pointers documented as "device" must point to memory of the current
+ *     CUDA device, 16-byte aligned; the caller owns them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it and return without synchronising
+ *     unless stated otherwise.
+ *   - A plan is not thread-safe: concurrent calls on one plan, or calls on
+ *     one plan from different streams without ordering, race on its scratch.
+ *
+ * State layout in device memory
+ *   SWEPT_F64  : double u[N].
+ *   SWEPT_F32C : float hi[N] followed by float lo[N] (8N bytes); the value
+ *                of point i is hi[i] + lo[i] (compensated FP32).
+ */
+#ifndef SWEPT_H
+#define SWEPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- enums ------------------------------------------------------------ */
+
+/* Arithmetic of the state (Section 2 leaves precision open). */
+#define SWEPT_F64   0   /* IEEE binary64 */
+#define SWEPT_F32C  1   /* binary32 pair (hi, lo), TwoSum-compensated update */
+
+/* Stencils (the sub-timestep of Section 2, one per time level).
+ *   SWEPT_HEAT: u_t = u_xx, 3-point forward Euler; radius 1;
+ *               params[0] = r = dt/dx^2.
+ *   SWEPT_KS  : u_t = -u u_x - u_xx - u_xxxx (Section 6), central
+ *               differences with flux u^2/2 and the 3-point second
+ *               difference applied twice, forward Euler; radius 2;
+ *               params[0] = dt, params[1] = dx.                            */
+#define SWEPT_HEAT  0
+#define SWEPT_KS    1
+
+/* Status codes. */
+#define SWEPT_OK         0
+#define SWEPT_EINVAL    -1   /* bad argument: sizes, radius, null pointer   */
+#define SWEPT_ENOMEM    -2   /* device allocation failed                    */
+#define SWEPT_ECUDA     -3   /* a CUDA call or kernel launch failed         */
+#define SWEPT_ETIMEOUT  -4   /* a device-side wait ran out (batched launch) */
+#define SWEPT_ENOTSUP   -5   /* combination not built into this library     */
+
+/* Reductions for swept_reduce. */
+#define SWEPT_SUM         0  /* sum_i u_i                 (Section 6 check) */
+#define SWEPT_HALF_SUMSQ  1  /* J = 1/2 sum_i u_i^2                         */
+#define SWEPT_DOT         2  /* sum_i u_i v_i                               */
+
+typedef struct swept_plan_s *swept_plan_t;
+
+/* ---- plan ------------------------------------------------------------- */
+
+/*
+ * swept_plan -- validate a problem and allocate its scratch.
+ *
+ * Defines the problem of Section 3: a periodic 1D grid of N points split
+ * into N/B tiles of B points, each advanced by the stencil `stencil_id`
+ * (radius `radius`, parameters `params[0..nparams)`) in arithmetic `dtype`.
+ *   N       >= B, N % B == 0.
+ *   radius  must equal the stencil's radius (1 heat, 2 KS).
+ *   B       tile width: 32*K points with K in {1,2,4,8,16,32}, K % radius
+ *           == 0 (Section 3 asks for an even number of points per node; in
+ *           general B % (2*radius) == 0).  B = 0 picks the tuned default.
+ *   params  host pointer; copied.
+ * Allocates the edge double-buffer (2 * 2N values, 32N bytes) on the
+ * current device.  *out is set on success.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP, SWEPT_ENOMEM, SWEPT_ECUDA.
+ */
+int swept_plan(swept_plan_t *out, int64_t N, int radius, int stencil_id,
+               const double *params, int nparams, int dtype, int B);
+
+/* Release the plan and its device scratch (synchronises the device). */
+void swept_destroy(swept_plan_t plan);
+
+/* Query: B, h = B/(2 radius), N, dtype, stencil, radius in info[0..6). */
+int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
+
+/* ---- advance ---------------------------------------------------------- */
+
+/*
+ * swept_advance -- u <- u after nsteps sub-timesteps, by the swept rule.
+ *
+ * Stage 0 is the shrinking triangle of Section 3 on the tiles [jB, jB+B);
+ * every later stage is a diamond on the windows shifted by B/2 from the
+ * previous stage's (the alternating point sets of Section 3), started from
+ * the V of leading edges that the two neighbouring triangles wrote to the
+ * plan's edge buffer.  nsteps = q*h + rem (h = B/(2 radius)) takes q + 1
+ * launches when rem == 0, q + 2 otherwise (the last stage ends with a
+ * trapezoid of height rem and its fill).
+ *   u       device, state layout of the plan's dtype, overwritten in place.
+ *   nsteps  >= 0; 0 is a no-op.
+ * Errors: SWEPT_EINVAL (null plan/u, nsteps < 0), SWEPT_ECUDA.
+ */
+int swept_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream);
+
+/*
+ * swept_naive_advance -- the same result by per-step stepping: one kernel
+ * launch and one full read and write of u per sub-timestep (the "straight"
+ * decomposition that Section 6 compares against).  Uses the plan's scratch
+ * as the second buffer.  Same arguments and errors as swept_advance.
+ */
+int swept_naive_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream);
+
+/* ---- FP32-compensated state conversion -------------------------------- */
+
+/*
+ * swept_f32c_split -- hi = fl32(u), lo = fl32(u - hi) for N points.
+ *   u64  device double[N];  u32c device float[2N] (hi then lo).
+ * swept_f32c_merge -- u = (double)hi + (double)lo.
+ * Errors: SWEPT_EINVAL, SWEPT_ECUDA.
+ */
+int swept_f32c_split(int64_t N, const double *u64, void *u32c, void *stream);
+int swept_f32c_merge(int64_t N, const void *u32c, double *u64, void *stream);
+
+/* ---- reductions -------------------------------------------------------- */
+
+/*
+ * swept_reduce -- FP64 reduction of the state (conserved sum, objective J,
+ * or the directional derivative <u, v>).  Compensated (TwoSum/TwoProd)
+ * accumulation in a fixed order, so repeated calls give identical bits.
+ *   u    device state in the plan's layout (F32C values enter as
+ *        fl64(hi + lo)).
+ *   what SWEPT_SUM, SWEPT_HALF_SUMSQ or SWEPT_DOT.
+ *   v    device double[N] for SWEPT_DOT, else ignored.
+ *   out  device double[1]: the result is written there (no host sync).
+ * Errors: SWEPT_EINVAL, SWEPT_ECUDA.
+ */
+int swept_reduce(swept_plan_t plan, const void *u, int what, const void *v,
+                 double *out, void *stream);
+
+/* ---- diagnostics ------------------------------------------------------ */
+
+/* Name of a status code (static string). */
+const char *swept_strerror(int code);
+
+/* Library build identification: "<version> sm_103a". */
+const char *swept_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWEPT_H */

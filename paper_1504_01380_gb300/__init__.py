@@ -1,0 +1,196 @@
+"""Python binding of the swept-rule CUDA library (``include/swept.h``).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  The functions keep the
+C names; errors raise ``SweptError`` with the library's message.  The
+library must have been built (``python -m paper_1504_01380_gb300.build``);
+nothing here falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
+
+SWEPT_F64, SWEPT_F32C = 0, 1
+SWEPT_HEAT, SWEPT_KS = 0, 1
+SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT = 0, 1, 2
+SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP = 0, -1, -2, -3, -4, -5
+
+RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2}
+
+# Every entry point declared in include/swept.h.
+EXPORTS = (
+    "swept_plan", "swept_destroy", "swept_plan_info", "swept_advance", "swept_naive_advance",
+    "swept_f32c_split", "swept_f32c_merge", "swept_reduce", "swept_strerror", "swept_version",
+)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SweptError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+def load(path: str | None = None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"swept CUDA library not built: {p} is missing "
+                               "(run python -m paper_1504_01380_gb300.build)")
+        L = ctypes.CDLL(p)
+        vp, i64, i32, dbl_p = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+        L.swept_plan.argtypes = [ctypes.POINTER(vp), i64, i32, i32, ctypes.POINTER(ctypes.c_double),
+                                 i32, i32, i32]
+        L.swept_plan.restype = i32
+        L.swept_destroy.argtypes = [vp]
+        L.swept_destroy.restype = None
+        L.swept_plan_info.argtypes = [vp, ctypes.POINTER(i64), i32]
+        L.swept_plan_info.restype = i32
+        for f in ("swept_advance", "swept_naive_advance"):
+            getattr(L, f).argtypes = [vp, vp, i64, vp]
+            getattr(L, f).restype = i32
+        L.swept_f32c_split.argtypes = [i64, vp, vp, vp]
+        L.swept_f32c_split.restype = i32
+        L.swept_f32c_merge.argtypes = [i64, vp, vp, vp]
+        L.swept_f32c_merge.restype = i32
+        L.swept_reduce.argtypes = [vp, vp, i32, vp, dbl_p, vp]
+        L.swept_reduce.restype = i32
+        L.swept_strerror.argtypes = [i32]
+        L.swept_strerror.restype = ctypes.c_char_p
+        L.swept_version.argtypes = []
+        L.swept_version.restype = ctypes.c_char_p
+        _lib = L
+        return _lib
+
+
+def strerror(code: int) -> str:
+    return load().swept_strerror(int(code)).decode()
+
+
+def swept_version() -> str:
+    return load().swept_version().decode()
+
+
+def _check(rc: int, what: str):
+    if rc != SWEPT_OK:
+        raise SweptError(rc, what)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_ptr(t, nbytes: int, what: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if t.numel() * t.element_size() < nbytes:
+        raise ValueError(f"{what}: tensor holds {t.numel() * t.element_size()} bytes, needs {nbytes}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A validated problem with its device scratch (``swept_plan`` / ``swept_destroy``)."""
+
+    def __init__(self, handle, N, stencil, dtype, B, H, params):
+        self._h = handle
+        self.N, self.stencil, self.dtype, self.B, self.h = N, stencil, dtype, B, H
+        self.radius = RADIUS[stencil]
+        self.params = tuple(params)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("plan was destroyed")
+        return self._h
+
+    @property
+    def state_bytes(self) -> int:
+        return 8 * self.N
+
+    def destroy(self):
+        if self._h is not None:
+            load().swept_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def swept_plan(N: int, radius: int, stencil_id: int, params, dtype: int, B: int = 0) -> Plan:
+    L = load()
+    prm = (ctypes.c_double * len(params))(*[float(x) for x in params])
+    h = ctypes.c_void_p()
+    _check(L.swept_plan(ctypes.byref(h), int(N), int(radius), int(stencil_id), prm, len(params),
+                        int(dtype), int(B)), "swept_plan")
+    info = (ctypes.c_int64 * 6)()
+    _check(L.swept_plan_info(h, info, 6), "swept_plan_info")
+    return Plan(h, int(N), int(stencil_id), int(dtype), int(info[0]), int(info[1]), params)
+
+
+def swept_advance(plan: Plan, u, nsteps: int, stream=None):
+    """u <- u after nsteps sub-timesteps (swept rule), in place on ``stream``."""
+    _check(load().swept_advance(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(nsteps),
+                                _stream(stream)), "swept_advance")
+    return u
+
+
+def swept_naive_advance(plan: Plan, u, nsteps: int, stream=None):
+    """Same result by per-step stepping (one launch per sub-timestep)."""
+    _check(load().swept_naive_advance(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(nsteps),
+                                      _stream(stream)), "swept_naive_advance")
+    return u
+
+
+def swept_f32c_split(u64, out=None, stream=None):
+    """FP64 tensor -> compensated FP32 state tensor (hi then lo, float32[2N])."""
+    import torch
+    n = u64.numel()
+    if u64.dtype != torch.float64:
+        raise TypeError("swept_f32c_split: expected float64")
+    if out is None:
+        out = torch.empty(2 * n, dtype=torch.float32, device=u64.device)
+    _check(load().swept_f32c_split(n, _dev_ptr(u64, 8 * n, "u64"), _dev_ptr(out, 8 * n, "u32c"),
+                                   _stream(stream)), "swept_f32c_split")
+    return out
+
+
+def swept_f32c_merge(u32c, out=None, stream=None):
+    """Compensated FP32 state tensor -> FP64 tensor of hi + lo."""
+    import torch
+    n = u32c.numel() // 2
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=u32c.device)
+    _check(load().swept_f32c_merge(n, _dev_ptr(u32c, 8 * n, "u32c"), _dev_ptr(out, 8 * n, "u64"),
+                                   _stream(stream)), "swept_f32c_merge")
+    return out
+
+
+def swept_reduce(plan: Plan, u, what: int, v=None, out=None, stream=None):
+    """FP64 reduction of the state into a 1-element device tensor (no host sync)."""
+    import torch
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+    vp = _dev_ptr(v, 8 * plan.N, "v") if v is not None else ctypes.c_void_p(0)
+    _check(load().swept_reduce(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(what), vp,
+                               _dev_ptr(out, 8, "out"), _stream(stream)), "swept_reduce")
+    return out

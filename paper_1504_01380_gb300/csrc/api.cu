@@ -1,0 +1,232 @@
+// C ABI of the swept-rule library (see include/swept.h for the contract).
+//
+// The plan owns the device scratch: the leading-edge double buffer (the
+// "messages" of Section 3, written by one stage and read by the next) and
+// the reduction partials.  swept_advance turns nsteps into the stage
+// schedule and enqueues one stage kernel per stage on the caller's stream.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "swept.h"
+#include "swept_internal.h"
+
+using swept::Consts;
+using swept::StageArgs;
+
+struct swept_plan_s {
+  int64_t N;
+  int radius, stencil, dtype, B, K, H, nwin, device;
+  double prm[2];
+  Consts c;
+  unsigned char* edges;   // two buffers of nwin * 2B elements of 8 bytes
+  size_t edge_half;       // bytes per buffer
+  double* red;            // 2 * kReduceBlocks partials
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SWEPT_OK;
+  if (e == cudaErrorMemoryAllocation) return SWEPT_ENOMEM;
+  return SWEPT_ECUDA;
+}
+
+// Constants of the update.  heat: r.  KS: a = -(dt/(4 dx)), b = -(dt/dx^2),
+// e = -(dt/(dx^2 dx^2)), evaluated in FP64 in this order; FP32 copies are
+// the FP64 values rounded to nearest.
+int make_consts(int stencil, const double* p, int np, Consts& c) {
+  std::memset(&c, 0, sizeof c);
+  if (stencil == SWEPT_HEAT) {
+    if (np < 1) return SWEPT_EINVAL;
+    c.r = p[0];
+    c.r32 = (float)c.r;
+    return SWEPT_OK;
+  }
+  if (stencil == SWEPT_KS) {
+    if (np < 2 || !(p[1] > 0.0)) return SWEPT_EINVAL;
+    const double dt = p[0], dx = p[1];
+    const double dx2 = dx * dx;
+    c.a = -(dt / (4.0 * dx));
+    c.b = -(dt / dx2);
+    c.e = -(dt / (dx2 * dx2));
+    c.a32 = (float)c.a;
+    c.b32 = (float)c.b;
+    c.e32 = (float)c.e;
+    return SWEPT_OK;
+  }
+  return SWEPT_EINVAL;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
+  if (p->stencil == SWEPT_HEAT)
+    return p->dtype == SWEPT_F64 ? swept::launch_stage_heat_f64(p->K, a, s)
+                                 : swept::launch_stage_heat_f32c(p->K, a, s);
+  return p->dtype == SWEPT_F64 ? swept::launch_stage_ks_f64(p->K, a, s)
+                               : swept::launch_stage_ks_f32c(p->K, a, s);
+}
+
+// Default tile width: the largest of 512, 256, ... that divides N and keeps
+// K a multiple of the radius.
+int default_B(int64_t N, int radius) {
+  for (int K = 16; K >= 1; K /= 2) {
+    const int B = 32 * K;
+    if (K % radius == 0 && N % B == 0) return B;
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* swept_strerror(int code) {
+  switch (code) {
+    case SWEPT_OK: return "ok";
+    case SWEPT_EINVAL: return "invalid argument";
+    case SWEPT_ENOMEM: return "out of device memory";
+    case SWEPT_ECUDA: return "CUDA error";
+    case SWEPT_ETIMEOUT: return "device-side wait timed out";
+    case SWEPT_ENOTSUP: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+const char* swept_version(void) { return "swept 0.1 sm_103a"; }
+
+int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const double* params,
+               int nparams, int dtype, int B) {
+  if (!out || !params) return SWEPT_EINVAL;
+  *out = nullptr;
+  if (stencil_id != SWEPT_HEAT && stencil_id != SWEPT_KS) return SWEPT_EINVAL;
+  const int rad = stencil_id == SWEPT_HEAT ? 1 : 2;
+  if (radius != rad) return SWEPT_EINVAL;
+  if (dtype != SWEPT_F64 && dtype != SWEPT_F32C) return SWEPT_EINVAL;
+  if (N <= 0) return SWEPT_EINVAL;
+  if (B == 0) B = default_B(N, rad);
+  if (B <= 0 || B % 32) return SWEPT_EINVAL;
+  const int K = B / 32;
+  if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32) return SWEPT_ENOTSUP;
+  if (K % rad) return SWEPT_EINVAL;
+  if (N % B) return SWEPT_EINVAL;
+  if (N / B > (int64_t)0x7fffffff) return SWEPT_EINVAL;
+  Consts c;
+  int st = make_consts(stencil_id, params, nparams, c);
+  if (st) return st;
+
+  swept_plan_s* p = (swept_plan_s*)std::calloc(1, sizeof(swept_plan_s));
+  if (!p) return SWEPT_ENOMEM;
+  p->N = N;
+  p->radius = rad;
+  p->stencil = stencil_id;
+  p->dtype = dtype;
+  p->B = B;
+  p->K = K;
+  p->H = B / (2 * rad);
+  p->nwin = (int)(N / B);
+  p->prm[0] = params[0];
+  p->prm[1] = nparams > 1 ? params[1] : 0.0;
+  p->c = c;
+  cudaGetDevice(&p->device);
+  p->edge_half = (size_t)p->nwin * 2 * B * 8;
+  cudaError_t e = cudaMalloc((void**)&p->edges, 2 * p->edge_half);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->red, 2 * swept::kReduceBlocks * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (p->edges) cudaFree(p->edges);
+    std::free(p);
+    return cuda_status(e);
+  }
+  *out = p;
+  return SWEPT_OK;
+}
+
+void swept_destroy(swept_plan_t p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  if (p->edges) cudaFree(p->edges);
+  if (p->red) cudaFree(p->red);
+  std::free(p);
+}
+
+int swept_plan_info(swept_plan_t p, int64_t* info, int ninfo) {
+  if (!p || !info) return SWEPT_EINVAL;
+  const int64_t v[6] = {p->B, p->H, p->N, p->dtype, p->stencil, p->radius};
+  for (int i = 0; i < ninfo && i < 6; ++i) info[i] = v[i];
+  return SWEPT_OK;
+}
+
+int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
+  if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
+  if (nsteps == 0) return SWEPT_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t H = p->H;
+  const int64_t q = nsteps / H;
+  const int rem = (int)(nsteps % H);
+  unsigned char* buf[2] = {p->edges, p->edges + p->edge_half};
+  StageArgs a;
+  a.u = u;
+  a.N = p->N;
+  a.nwin = p->nwin;
+  a.c = p->c;
+  // stage k: windows shifted by B/2 when k is odd (the alternating point
+  // sets of Section 3); reads the edges of stage k-1, writes its own.
+  auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
+    a.offset = (k & 1) ? p->B / 2 : 0;
+    a.hv = hv;
+    a.ht = ht;
+    a.ein = buf[(k + 1) & 1];
+    a.eout = buf[k & 1];
+    return launch_stage(p, a, s);
+  };
+  cudaError_t e = cudaSuccess;
+  if (q == 0) {
+    e = stage(0, 0, rem);                              // trapezoid of height rem
+    if (e == cudaSuccess) e = stage(1, rem, 0);       // its V-fill
+  } else {
+    e = stage(0, 0, (int)H);                           // shrinking triangles
+    for (int64_t k = 1; k < q && e == cudaSuccess; ++k) e = stage(k, (int)H, (int)H);   // diamonds
+    if (e == cudaSuccess) e = stage(q, (int)H, rem);  // last V-fill (+ trapezoid)
+    if (e == cudaSuccess && rem > 0) e = stage(q + 1, rem, 0);
+  }
+  return cuda_status(e);
+}
+
+int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
+  if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* bufs[2] = {u, p->edges};
+  cudaError_t e = cudaSuccess;
+  int cur = 0;
+  for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+    e = swept::launch_naive_step(p->stencil, p->dtype, bufs[cur], bufs[cur ^ 1], p->N, p->c, s);
+    cur ^= 1;
+  }
+  if (e == cudaSuccess && cur == 1) {
+    const size_t bytes = (size_t)p->N * 8;   // F64: N doubles; F32C: 2N floats
+    e = cudaMemcpyAsync(u, p->edges, bytes, cudaMemcpyDeviceToDevice, s);
+  }
+  return cuda_status(e);
+}
+
+int swept_f32c_split(int64_t N, const double* u64, void* u32c, void* stream) {
+  if (N <= 0 || !u64 || !u32c) return SWEPT_EINVAL;
+  return cuda_status(swept::launch_split(N, u64, (float*)u32c, (cudaStream_t)stream));
+}
+
+int swept_f32c_merge(int64_t N, const void* u32c, double* u64, void* stream) {
+  if (N <= 0 || !u64 || !u32c) return SWEPT_EINVAL;
+  return cuda_status(swept::launch_merge(N, (const float*)u32c, u64, (cudaStream_t)stream));
+}
+
+int swept_reduce(swept_plan_t p, const void* u, int what, const void* v, double* out, void* stream) {
+  if (!p || !u || !out) return SWEPT_EINVAL;
+  if (what < SWEPT_SUM || what > SWEPT_DOT) return SWEPT_EINVAL;
+  if (what == SWEPT_DOT && !v) return SWEPT_EINVAL;
+  return cuda_status(swept::launch_reduce(p->dtype, u, what, (const double*)v, p->N, p->red, out,
+                                          (cudaStream_t)stream));
+}
+
+}  // extern "C"

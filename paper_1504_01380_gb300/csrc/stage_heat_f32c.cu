@@ -1,0 +1,8 @@
+// Instantiation of the swept stage kernel: heat, f32c.
+#include "swept_stage.cuh"
+
+namespace swept {
+cudaError_t launch_stage_heat_f32c(int K, const StageArgs& a, cudaStream_t s) {
+  return launch_stage_dispatch<kHeat, F32C>(K, a, s);
+}
+}  // namespace swept

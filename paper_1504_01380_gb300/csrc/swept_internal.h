@@ -1,0 +1,48 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "swept_device.cuh"
+
+namespace swept {
+
+// Warps per thread block of the stage kernels.  One warp owns one window.
+constexpr int kWarpsPerBlock = 4;
+
+// Arguments of one swept stage launch (one window per warp).
+struct StageArgs {
+  void* u;             // flat state (F64 double[N]; F32C float hi[N], lo[N])
+  const void* ein;     // leading edges of the previous stage: nwin * 2B elements
+  void* eout;          // leading edges written by this stage
+  int64_t N;
+  int nwin;            // N / B windows
+  int offset;          // 0: windows [wB, wB+B); B/2: windows shifted right by B/2
+  int hv;              // V-fill height (0 = load the flat state instead)
+  int ht;              // trapezoid height (0 = none; h = full triangle)
+  Consts c;
+};
+
+// Launchers, one per (stencil, dtype); K = B / 32.
+cudaError_t launch_stage_heat_f64(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_heat_f32c(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ks_f64(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ks_f32c(int K, const StageArgs& a, cudaStream_t s);
+
+// Shared-memory bytes per block of the stage kernel for tile width B.
+inline size_t stage_smem_bytes(int B) { return (size_t)kWarpsPerBlock * 2 * B * 8; }
+
+// Naive per-step stepper: out = S(in).
+cudaError_t launch_naive_step(int stencil, int dtype, const void* in, void* out, int64_t N,
+                              const Consts& c, cudaStream_t s);
+
+// Conversion and reductions.
+cudaError_t launch_split(int64_t N, const double* u64, float* u32c, cudaStream_t s);
+cudaError_t launch_merge(int64_t N, const float* u32c, double* u64, cudaStream_t s);
+// scratch: at least 2 * kReduceBlocks doubles.
+constexpr int kReduceBlocks = 304;
+cudaError_t launch_reduce(int dtype, const void* u, int what, const double* v, int64_t N,
+                          double* scratch, double* out, cudaStream_t s);
+
+}  // namespace swept

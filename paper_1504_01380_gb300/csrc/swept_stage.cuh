@@ -1,0 +1,240 @@
+// The swept stage kernel (Section 3): one warp advances one window of
+// B = 32*K points whose values live in registers, K consecutive points per
+// lane.  Neighbour values inside the window come from the adjacent lanes by
+// warp shuffle; the window exchanges only its leading edges, through global
+// memory, between launches.
+//
+// A stage is up to two phases on the same window:
+//
+//   V-fill (height hv): the window starts from the V formed by the right
+//   leading edge of the window on its left and the left leading edge of the
+//   window on its right, both written by the previous stage.  Level m
+//   (m = 1..hv) computes the gap [B/2 - r m, B/2 + r m) around the window's
+//   centre from level m-1: the previous gap plus 2r edge values on each
+//   side, placed into the registers that hold those points just before the
+//   level.  With hv = h = B/(2r) the gap fills the whole window: a flat level.
+//
+//   Trapezoid (height ht): from a flat window, level m (m = 1..ht) is
+//   computable on [r m, B - r m), the shrinking triangle.  After level m is
+//   computed its leading edges are kept: the 2r left-most values
+//   [r m, r m + 2r) and the 2r right-most values [B - r m - 2r, B - r m), for
+//   m = 0..ht-1 (Section 3: "two left-most outputs of every sub-timestep"
+//   for a 3-point stencil).  With ht = h the top level is 2r points wide.
+//
+// Every lane computes all its K points at every level; points outside the
+// computable interval get values that nothing reads later (they are either
+// overwritten by a placement or never read again).  Placements and captures
+// happen at compile-time register offsets: levels are processed in phases
+// of K/r levels, during which the interval boundary stays in one lane and
+// moves r registers per level.
+//
+// Layout of one window's edges in global memory (elements of type E):
+//   [ L[0][0..2r) L[1][..] ... L[h-1][..] | R[0][0..2r) ... R[h-1][..] ]
+// i.e. 2B elements per window, window w at offset w*2B.
+#pragma once
+
+#include "swept_internal.h"
+
+namespace swept {
+
+template <int ST, class DT, int K>
+struct StageImpl {
+  using E = typename DT::E;
+  using C = typename DT::C;
+  static constexpr int R = Radius<ST>::value;
+  static constexpr int B = 32 * K;
+  static constexpr int H = B / (2 * R);
+  static constexpr int L = K / R;      // levels per phase
+  static_assert(K % R == 0, "K must be a multiple of the stencil radius");
+
+  // Levels 1..hv of the V-fill; sL / sR hold the arms (level-major, 2r each).
+  static __device__ __forceinline__ void vfill(Tile<DT, K>& t, const E* sL, const E* sR, int hv,
+                                               int lane, const Consts& c) {
+    const int hmain = hv < H ? hv : H - 1;
+    for (int P = 0; P * L < hmain; ++P) {
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        const int mp = P * L + j;            // level mp values are placed, mp+1 computed
+        if (mp >= hmain) break;
+        // left arm, positions 16K - R*mp - 2R + q
+#pragma unroll
+        for (int q = 0; q < 2 * R; ++q) {
+          const int cc = K - R * j - 2 * R + q;
+          const int dl = cc < 0 ? 1 : 0;
+          const int k = cc < 0 ? cc + K : cc;
+          const E v = sL[mp * 2 * R + q];
+          if (lane == 15 - P - dl) t.put(k, v);
+        }
+        // right arm, positions 16K + R*mp + q
+#pragma unroll
+        for (int q = 0; q < 2 * R; ++q) {
+          const int cc = R * j + q;
+          const int dr = cc >= K ? 1 : 0;
+          const int k = cc - dr * K;
+          const E v = sR[mp * 2 * R + q];
+          if (lane == 16 + P + dr) t.put(k, v);
+        }
+        tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr);
+      }
+    }
+    if (hv == H) {
+      // Last level: the arms reach r points beyond the window on each side.
+      // Their inner halves go to lanes 0 and 31, their outer halves become
+      // the halo of lane 0 (positions -r..-1) and lane 31 (B..B+r-1).
+      const int mp = H - 1;
+      C ovl[R], ovr[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        ovl[q] = Tile<DT, K>::hi_of(sL[mp * 2 * R + q]);
+        const E vl = sL[mp * 2 * R + R + q];
+        if (lane == 0) t.put(q, vl);
+        const E vr = sR[mp * 2 * R + q];
+        if (lane == 31) t.put(K - R + q, vr);
+        ovr[q] = Tile<DT, K>::hi_of(sR[mp * 2 * R + R + q]);
+      }
+      tile_level<ST, DT, K, true>(t, c, lane, ovl, ovr);
+    }
+  }
+
+  // Levels 1..ht of the shrinking triangle; edges of levels 0..ht-1 go to
+  // oL / oR.  On return the tile holds level ht-1 (the caller computes the
+  // top level when ht < h).
+  static __device__ __forceinline__ void trapezoid(Tile<DT, K>& t, E* oL, E* oR, int ht, int lane,
+                                                   const Consts& c) {
+    for (int P = 0; P * L < ht; ++P) {
+#pragma unroll
+      for (int j = 0; j < L; ++j) {
+        const int m = P * L + j;
+        if (m >= ht) break;
+        if (m > 0) tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr);
+        // left edge: positions P*K + R*j + q
+#pragma unroll
+        for (int q = 0; q < 2 * R; ++q) {
+          const int cc = R * j + q;
+          const int dl = cc >= K ? 1 : 0;
+          const int k = cc - dl * K;
+          if (lane == P + dl) oL[m * 2 * R + q] = t.get(k);
+        }
+        // right edge: positions (31 - P)*K + K - R*j - 2R + q
+#pragma unroll
+        for (int q = 0; q < 2 * R; ++q) {
+          const int cc = K - R * j - 2 * R + q;
+          const int dr = cc < 0 ? 1 : 0;
+          const int k = cc + dr * K;
+          if (lane == 31 - P - dr) oR[m * 2 * R + q] = t.get(k);
+        }
+      }
+    }
+  }
+
+  // Copy n elements (n even, 8-byte elements, 16-byte aligned) with the warp.
+  static __device__ __forceinline__ void warp_copy(E* __restrict__ dst, const E* __restrict__ src,
+                                                   int n, int lane) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (int i = lane; i < n / 2; i += 32) d4[i] = s4[i];
+  }
+
+  static __device__ void run(const StageArgs& a, E* sm) {
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (w >= a.nwin) return;                     // warp-uniform
+    const int64_t N = a.N;
+    const int64_t ws = (int64_t)w * B + a.offset;  // window start, < N
+    E* sL = sm;
+    E* sR = sm + B;
+    Tile<DT, K> t;
+    t.zero();
+    if (a.hv == 0) {
+      int64_t g = ws + (int64_t)lane * K;
+      if (g >= N) g -= N;                        // wrap falls on a lane boundary
+      load_points<K>(t, a.u, N, g);
+    } else {
+      const int wl = a.offset ? w : (w == 0 ? a.nwin - 1 : w - 1);
+      const int wr = a.offset ? (w + 1 == a.nwin ? 0 : w + 1) : w;
+      const E* ein = static_cast<const E*>(a.ein);
+      warp_copy(sL, ein + (int64_t)wl * (2 * B) + B, a.hv * 2 * R, lane);
+      warp_copy(sR, ein + (int64_t)wr * (2 * B), a.hv * 2 * R, lane);
+      __syncwarp();
+      vfill(t, sL, sR, a.hv, lane, a.c);
+      __syncwarp();
+    }
+    if (a.ht > 0) {
+      trapezoid(t, sL, sR, a.ht, lane, a.c);
+      __syncwarp();
+      E* eout = static_cast<E*>(a.eout) + (int64_t)w * (2 * B);
+      warp_copy(eout, sL, a.ht * 2 * R, lane);
+      warp_copy(eout + B, sR, a.ht * 2 * R, lane);
+      if (a.ht < H) {
+        // top of the trapezoid: level ht on [r ht, B - r ht)
+        tile_level<ST, DT, K, false>(t, a.c, lane, nullptr, nullptr);
+        const int lo = R * a.ht, hi = B - R * a.ht;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int x = lane * K + k;
+          if (x >= lo && x < hi) {
+            int64_t g = ws + x;
+            if (g >= N) g -= N;
+            store_point<K>(t, k, a.u, N, g);
+          }
+        }
+      }
+    } else if (a.hv == H) {
+      int64_t g = ws + (int64_t)lane * K;
+      if (g >= N) g -= N;
+      store_points<K>(t, a.u, N, g);
+    } else {
+      // partial V-fill: its gap [B/2 - r hv, B/2 + r hv) is at level hv
+      const int lo = B / 2 - R * a.hv, hi = B / 2 + R * a.hv;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int x = lane * K + k;
+        if (x >= lo && x < hi) {
+          int64_t g = ws + x;
+          if (g >= N) g -= N;
+          store_point<K>(t, k, a.u, N, g);
+        }
+      }
+    }
+  }
+};
+
+template <int ST, class DT, int K>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+swept_stage_kernel(const StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using E = typename DT::E;
+  constexpr int B = 32 * K;
+  E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * B);
+  StageImpl<ST, DT, K>::run(a, sm);
+}
+
+template <int ST, class DT, int K>
+cudaError_t launch_stage_k(const StageArgs& a, cudaStream_t s) {
+  constexpr int B = 32 * K;
+  const size_t smem = stage_smem_bytes(B);
+  // set on every launch: the attribute belongs to the current device
+  cudaError_t e = cudaFuncSetAttribute(swept_stage_kernel<ST, DT, K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (a.nwin + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  swept_stage_kernel<ST, DT, K><<<grid, kWarpsPerBlock * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int ST, class DT>
+cudaError_t launch_stage_dispatch(int K, const StageArgs& a, cudaStream_t s) {
+  switch (K) {
+    case 1:
+      if constexpr (Radius<ST>::value == 1) return launch_stage_k<ST, DT, 1>(a, s);
+      else return cudaErrorInvalidValue;
+    case 2: return launch_stage_k<ST, DT, 2>(a, s);
+    case 4: return launch_stage_k<ST, DT, 4>(a, s);
+    case 8: return launch_stage_k<ST, DT, 8>(a, s);
+    case 16: return launch_stage_k<ST, DT, 16>(a, s);
+    case 32: return launch_stage_k<ST, DT, 32>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace swept

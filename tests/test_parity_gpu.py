@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA swept and naive steppers against the CPU oracle.
+
+Every comparison goes through the C ABI (the Python binding marshals only).
+FP64 and FP32-compensated results must be bit-exact against the oracle's
+per-step stepping of the same arithmetic (the swept rule only reorders the
+work); the compensated state is also compared with the FP64 oracle within a
+stated tolerance.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import reductions as ored
+
+pytestmark = pytest.mark.gpu
+
+HEAT, KS = 0, 1
+F64, F32C = 0, 1
+KS_PRM = (workloads.KS_DT, workloads.KS_DX)
+EPS = np.finfo(np.float64).eps
+
+
+def params_of(stencil):
+    return [workloads.HEAT_R] if stencil == HEAT else list(KS_PRM)
+
+
+def initial(stencil, n, seed):
+    return workloads.uniform(n, seed) if stencil == HEAT else workloads.ks_smoothed(n, seed) * 10.0
+
+
+def to_device(sw, plan, u0):
+    import torch
+    if plan.dtype == F64:
+        return torch.tensor(u0, dtype=torch.float64, device="cuda")
+    hi, lo = oracle.split_f32c(u0)
+    return torch.tensor(np.concatenate([hi, lo]), dtype=torch.float32, device="cuda")
+
+
+def from_device(plan, t):
+    a = t.cpu().numpy()
+    if plan.dtype == F64:
+        return a
+    return a[: plan.N], a[plan.N:]
+
+
+def oracle_run(stencil, dtype, u0, nsteps, threads=0):
+    if dtype == F64:
+        return oracle.advance_f64(stencil, params_of(stencil), u0, nsteps, threads)
+    hi, lo = oracle.split_f32c(u0)
+    return oracle.advance_f32c(stencil, params_of(stencil), hi, lo, nsteps, threads)
+
+
+def assert_same(plan, got, want):
+    if plan.dtype == F64:
+        bad = np.flatnonzero(got != want)
+        assert bad.size == 0, f"{bad.size} points differ, first at {bad[:5]}"
+    else:
+        for g, w in zip(got, want):
+            bad = np.flatnonzero(g != w)
+            assert bad.size == 0, f"{bad.size} points differ, first at {bad[:5]}"
+
+
+def run_gpu(sw, plan, u0, nsteps, naive=False):
+    import torch
+    u = to_device(sw, plan, u0)
+    (sw.swept_naive_advance if naive else sw.swept_advance)(plan, u, nsteps)
+    torch.cuda.synchronize()
+    return from_device(plan, u)
+
+
+CASES = [(st, dt, B) for st in (HEAT, KS) for dt in (F64, F32C) for B in (32, 64, 128, 256, 512, 1024)
+         if (B // 32) % (1 if st == HEAT else 2) == 0]
+
+
+@pytest.mark.parametrize("stencil,dtype,B", CASES)
+def test_swept_bit_exact_vs_oracle(cuda_lib, stencil, dtype, B):
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    h = B // (2 * r)
+    N = 8 * B
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, B)
+    u0 = initial(stencil, N, 1000 + B)
+    for nsteps in sorted({1, 2, h - 1, h, h + 1, 2 * h, 3 * h + h // 2 + 1}):
+        if nsteps < 1:
+            continue
+        got = run_gpu(sw, plan, u0, nsteps)
+        assert_same(plan, got, oracle_run(stencil, dtype, u0, nsteps))
+
+
+@pytest.mark.parametrize("stencil,dtype", [(s, d) for s in (HEAT, KS) for d in (F64, F32C)])
+def test_naive_bit_exact_vs_oracle(cuda_lib, stencil, dtype):
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    N = 64 * 37 * 4          # not a multiple of the 1024-point warp span: ragged last warp
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, 64)
+    u0 = initial(stencil, N, 77)
+    for nsteps in (1, 2, 7, 50):
+        assert_same(plan, run_gpu(sw, plan, u0, nsteps, naive=True),
+                    oracle_run(stencil, dtype, u0, nsteps))
+
+
+@pytest.mark.parametrize("stencil,dtype", [(s, d) for s in (HEAT, KS) for d in (F64, F32C)])
+def test_single_window_is_its_own_neighbour(cuda_lib, stencil, dtype):
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    B = 128
+    plan = sw.swept_plan(B, r, stencil, params_of(stencil), dtype, B)
+    u0 = initial(stencil, B, 5)
+    for nsteps in (1, 31, 32, 64, 100):
+        assert_same(plan, run_gpu(sw, plan, u0, nsteps), oracle_run(stencil, dtype, u0, nsteps))
+
+
+def test_zero_steps_is_identity(cuda_lib):
+    sw = cuda_lib
+    plan = sw.swept_plan(1024, 1, HEAT, [0.25], F64, 64)
+    u0 = workloads.uniform(1024, 3)
+    assert np.array_equal(run_gpu(sw, plan, u0, 0), u0)
+    assert np.array_equal(run_gpu(sw, plan, u0, 0, naive=True), u0)
+
+
+def test_heat_modes_1024_b32(cuda_lib):
+    """N = 1024, r = 1/4, 2000 steps, B = 32: bit-exact and on the closed form."""
+    sw = cuda_lib
+    n, nsteps = 1024, 2000
+    plan = sw.swept_plan(n, 1, HEAT, [0.25], F64, 32)
+    u0 = workloads.heat_modes(n, 8)
+    got = run_gpu(sw, plan, u0, nsteps)
+    assert np.array_equal(got, oracle.advance_f64(HEAT, [0.25], u0, nsteps))
+    k = np.arange(n // 2 + 1)
+    g = 1.0 - np.sin(np.pi * k / n) ** 2     # 1 - 4 r sin^2, r = 1/4
+    want = np.fft.irfft(np.fft.rfft(u0) * g ** nsteps, n)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(u0))
+
+
+def test_split_merge_bit_exact(cuda_lib):
+    import torch
+    sw = cuda_lib
+    u = workloads.uniform(100_000, 9) * 1e3
+    t = torch.tensor(u, device="cuda")
+    s = sw.swept_f32c_split(t)
+    hi, lo = oracle.split_f32c(u)
+    a = s.cpu().numpy()
+    assert np.array_equal(a[:100_000], hi) and np.array_equal(a[100_000:], lo)
+    m = sw.swept_f32c_merge(s).cpu().numpy()
+    assert np.array_equal(m, oracle.merge_f32c(hi, lo))
+
+
+@pytest.mark.parametrize("dtype", [F64, F32C])
+def test_reductions(cuda_lib, dtype):
+    import torch
+    sw = cuda_lib
+    N = 1 << 20
+    plan = sw.swept_plan(N, 1, HEAT, [0.25], dtype, 256)
+    u0 = workloads.heat_noise_modes(N, 16, 4)
+    v = workloads.uniform(N, 5)
+    u = to_device(sw, plan, u0)
+    vals = u0 if dtype == F64 else oracle.merge_f32c(*oracle.split_f32c(u0))
+    vt = torch.tensor(v, device="cuda")
+    got_sum = sw.swept_reduce(plan, u, sw.SWEPT_SUM).item()
+    got_j = sw.swept_reduce(plan, u, sw.SWEPT_HALF_SUMSQ).item()
+    got_dot = sw.swept_reduce(plan, u, sw.SWEPT_DOT, vt).item()
+    scale = np.sum(np.abs(vals))
+    assert abs(got_sum - ored.total(vals)) <= 4 * EPS * abs(ored.total(vals)) + N * EPS ** 2 * scale
+    assert abs(got_j - ored.half_sumsq(vals)) <= 4 * EPS * ored.half_sumsq(vals)
+    ex = ored.dot(vals, v)
+    assert abs(got_dot - ex) <= 4 * EPS * abs(ex) + N * EPS ** 2 * np.sum(np.abs(vals * v))
+    # deterministic: same bits again
+    assert sw.swept_reduce(plan, u, sw.SWEPT_HALF_SUMSQ).item() == got_j
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads, in the launch configuration the benchmark times
+# ---------------------------------------------------------------------------
+
+def oracle_point(stencil, dtype, u0, x, nsteps):
+    """u^nsteps at point x by the oracle, from the segment that point depends on."""
+    r = 1 if stencil == HEAT else 2
+    half = r * nsteps + r
+    idx = (x + np.arange(-half, half + 1)) % len(u0)
+    seg = u0[idx]
+    if dtype == F64:
+        return oracle.advance_f64(stencil, params_of(stencil), seg, nsteps)[half]
+    hi, lo = oracle.split_f32c(seg)
+    hi, lo = oracle.advance_f32c(stencil, params_of(stencil), hi, lo, nsteps)
+    return hi[half], lo[half]
+
+
+@pytest.mark.parametrize("dtype", [F64, F32C])
+def test_full_size_heat_2p24(cuda_lib, dtype):
+    """N = 2^24, 20000 steps, B = 512: swept == naive bit for bit, oracle samples, closed form."""
+    sw = cuda_lib
+    N, nsteps = 1 << 24, 20000
+    plan = sw.swept_plan(N, 1, HEAT, [0.25], dtype, 512)
+    u0 = workloads.heat_noise_modes(N)
+    got = run_gpu(sw, plan, u0, nsteps)
+    naive = run_gpu(sw, plan, u0, nsteps, naive=True)
+    assert_same(plan, got, naive)
+    rng = np.random.default_rng(0)
+    for x in [0, N - 1, 511, 512] + list(rng.integers(0, N, 2)):
+        want = oracle_point(HEAT, dtype, u0, int(x), nsteps)
+        if dtype == F64:
+            assert got[x] == want
+        else:
+            assert got[0][x] == want[0] and got[1][x] == want[1]
+    vals = got if dtype == F64 else got[0].astype(np.float64) + got[1].astype(np.float64)
+    k = np.arange(N // 2 + 1)
+    spec = np.fft.irfft(np.fft.rfft(u0) * (1.0 - np.sin(np.pi * k / N) ** 2) ** nsteps, N)
+    tol = 1e-11 if dtype == F64 else 1e-6
+    assert np.max(np.abs(vals - spec)) <= tol * np.max(np.abs(u0))
+
+
+@pytest.mark.parametrize("dtype", [F64, F32C])
+def test_full_size_ks_2p22(cuda_lib, dtype):
+    """KS N = 2^22, B = 256: 2000 steps against oracle samples; FP32C error vs FP64 oracle."""
+    sw = cuda_lib
+    N, nsteps = 1 << 22, 2000
+    plan = sw.swept_plan(N, 2, KS, list(KS_PRM), dtype, 256)
+    u0 = workloads.ks_smoothed(N)
+    got = run_gpu(sw, plan, u0, nsteps)
+    naive = run_gpu(sw, plan, u0, nsteps, naive=True)
+    assert_same(plan, got, naive)
+    for x in (0, N - 1, 255, 256, 1234567):
+        want = oracle_point(KS, dtype, u0, x, nsteps)
+        if dtype == F64:
+            assert got[x] == want
+        else:
+            assert got[0][x] == want[0] and got[1][x] == want[1]
+            ref = oracle_point(KS, F64, u0, x, nsteps)
+            val = float(got[0][x]) + float(got[1][x])
+            assert abs(val - ref) <= 1e-5 * max(abs(ref), 0.1)
