@@ -47,7 +47,7 @@ TILE_B = 512
 HEAT_R = 0.25
 METRIC = "cell-updates/s (N x steps / s), swept vs naive stepper, 1 GB300, at stated error"
 UNIT = "cell-updates/s"
-OPS_PER_UPDATE_F32C_HEAT = 9     # s, w, y, TwoSum (6): FP32 add/sub/mul/fma instructions
+OPS_PER_UPDATE_F32C_HEAT = 10    # 2 sub, add, fma, TwoSum (6): FP32 add/sub/mul/fma instructions
 OPS_PER_UPDATE_F64_HEAT = 3
 
 

@@ -35,10 +35,16 @@
  *     with a = -(dt/(4 dx)), b = -(dt/(dx dx)), e = -(dt/((dx dx)(dx dx))),
  *     computed here in FP64 in exactly that order.
  *
- *   FP32-compensated state (hi, lo), value = hi + lo:
- *       the stencil terms above are evaluated in FP32 on hi only,
- *       heat: y = fmaf(r, w, lo)
- *       KS:   y = fmaf(e, D, fmaf(b, w, fmaf(a, t, lo)))
+ *   FP32-compensated state (hi, lo), value = hi + lo.  The increment is
+ *   evaluated in FP32 on hi only, with differences taken first: h[j-1] - h[j]
+ *   is exact when neighbours are within a factor 2 (Sterbenz), so on smooth
+ *   data the second difference carries a relative, not an absolute, rounding
+ *   error (the sum form s - 2h loses |h|*2^-24 per step to cancellation):
+ *       heat: w = (h[i-1] - h[i]) + (h[i+1] - h[i]);  y = fmaf(r, w, lo)
+ *       KS:   W[j] = (h[j-1] - h[j]) + (h[j+1] - h[j]);
+ *             D = (W[i-1] - W[i]) + (W[i+1] - W[i]);
+ *             t = (h[i+1] - h[i-1]) * (h[i+1] + h[i-1])      (= G[i+1] - G[i-1])
+ *             y = fmaf(e, D, fmaf(b, W[i], fmaf(a, t, lo)))
  *       (hi', lo') = TwoSum(hi, y)           (Knuth, 6 operations)
  *     FP32 constants are the FP64 constants rounded to nearest.
  *     Split: hi = (float)u, lo = (float)(u - (double)hi);
@@ -175,19 +181,16 @@ static inline void point_f32c(const or_consts *c, const float *hi, const float *
     float h0 = hi[i];
     if (c->stencil == OR_HEAT) {
         float hm = hi[wrap(i - 1, n)], hp = hi[wrap(i + 1, n)];
-        float s = hm + hp;
-        float w = s - 2.0f * h0;
+        float w = (hm - h0) + (hp - h0);
         y = fmaf(c->r32, w, lo[i]);
     } else {
         float v[5];
         for (int k = -2; k <= 2; ++k) v[k + 2] = hi[wrap(i + k, n)];
-        float Gm = v[1] * v[1];
-        float Gp = v[3] * v[3];
-        float wm = (v[0] + v[2]) - 2.0f * v[1];
-        float w0 = (v[1] + v[3]) - 2.0f * v[2];
-        float wp = (v[2] + v[4]) - 2.0f * v[3];
-        float D = (wm + wp) - 2.0f * w0;
-        float t = Gp - Gm;
+        float wm = (v[0] - v[1]) + (v[2] - v[1]);
+        float w0 = (v[1] - v[2]) + (v[3] - v[2]);
+        float wp = (v[2] - v[3]) + (v[4] - v[3]);
+        float D = (wm - w0) + (wp - w0);
+        float t = (v[3] - v[1]) * (v[3] + v[1]);
         y = fmaf(c->e32, D, fmaf(c->b32, w0, fmaf(c->a32, t, lo[i])));
     }
     two_sum(h0, y, ho, lout);
