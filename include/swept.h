@@ -56,6 +56,8 @@ extern "C" {
 #define SWEPT_ECUDA     -3   /* a CUDA call or kernel launch failed         */
 #define SWEPT_ETIMEOUT  -4   /* a device-side wait ran out (batched launch) */
 #define SWEPT_ENOTSUP   -5   /* combination not built into this library     */
+#define SWEPT_ETOOBIG   -6   /* problem larger than swept_advance_noalloc's
+                                fixed scratch (N > SWEPT_NOALLOC_MAX_N)     */
 
 /* Reductions for swept_reduce. */
 #define SWEPT_SUM         0  /* sum_i u_i                 (Section 6 check) */
@@ -143,6 +145,37 @@ int swept_f32c_merge(int64_t N, const void *u32c, double *u64, void *stream);
  */
 int swept_reduce(swept_plan_t plan, const void *u, int what, const void *v,
                  double *out, void *stream);
+
+/* ---- advance without any device allocation ---------------------------- */
+
+/*
+ * swept_advance_noalloc -- swept_advance for callers that cannot allocate
+ * device memory (no plan, no cudaMalloc, no allocating library call).
+ *
+ * The paper has no counterpart: this is a deployment variant.  Some callers
+ * cannot call cudaMalloc -- a host that gives a plugin a fixed device-memory
+ * budget and forbids allocations after start-up, or code that must not take
+ * the implicit device synchronisation an allocation can cause.  This entry
+ * point keeps the leading-edge scratch in a fixed array in device global
+ * memory declared inside the library (32 * SWEPT_NOALLOC_MAX_N bytes =
+ * 32 MiB); every GPU that loads the library holds that array until the
+ * process exits.
+ *   N, stencil_id, params, nparams, dtype, B: as swept_plan (B must be given;
+ *           radius is implied by the stencil).  N <= SWEPT_NOALLOC_MAX_N,
+ *           else SWEPT_ETOOBIG.
+ *   u       device state, overwritten with u(nsteps), as swept_advance.
+ * Results are identical to swept_advance with the same arguments.
+ * All calls share the one array: calls that overlap on the GPU (different
+ * streams or host threads without ordering) race and corrupt each other.
+ * Nothing in the array needs to start at zero (each stage writes the edges
+ * the next stage reads).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and caches
+ * it; make that first call before any stream capture.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP, SWEPT_ETOOBIG, SWEPT_ECUDA.
+ */
+#define SWEPT_NOALLOC_MAX_N (1 << 20)
+int swept_advance_noalloc(int64_t N, int stencil_id, const double *params, int nparams,
+                          int dtype, int B, void *u, int64_t nsteps, void *stream);
 
 /* ---- diagnostics ------------------------------------------------------ */
 

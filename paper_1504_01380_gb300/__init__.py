@@ -19,6 +19,8 @@ SWEPT_F64, SWEPT_F32C = 0, 1
 SWEPT_HEAT, SWEPT_KS = 0, 1
 SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT = 0, 1, 2
 SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP = 0, -1, -2, -3, -4, -5
+SWEPT_ETOOBIG = -6
+SWEPT_NOALLOC_MAX_N = 1 << 20
 
 RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2}
 
@@ -26,6 +28,7 @@ RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2}
 EXPORTS = (
     "swept_plan", "swept_destroy", "swept_plan_info", "swept_advance", "swept_naive_advance",
     "swept_f32c_split", "swept_f32c_merge", "swept_reduce", "swept_strerror", "swept_version",
+    "swept_advance_noalloc",
 )
 
 _lock = threading.Lock()
@@ -66,6 +69,9 @@ def load(path: str | None = None):
         L.swept_f32c_merge.restype = i32
         L.swept_reduce.argtypes = [vp, vp, i32, vp, dbl_p, vp]
         L.swept_reduce.restype = i32
+        L.swept_advance_noalloc.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_double), i32, i32, i32,
+                                            vp, i64, vp]
+        L.swept_advance_noalloc.restype = i32
         L.swept_strerror.argtypes = [i32]
         L.swept_strerror.restype = ctypes.c_char_p
         L.swept_version.argtypes = []
@@ -194,3 +200,20 @@ def swept_reduce(plan: Plan, u, what: int, v=None, out=None, stream=None):
     _check(load().swept_reduce(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(what), vp,
                                _dev_ptr(out, 8, "out"), _stream(stream)), "swept_reduce")
     return out
+
+
+def swept_advance_noalloc(N: int, stencil_id: int, params, dtype: int, B: int, u, nsteps: int,
+                          stream=None):
+    """swept_advance without a plan and without any device allocation.
+
+    For callers that may not allocate device memory (a fixed memory budget
+    handed out by a host application, or code that must avoid the
+    synchronisation an allocation can cause).  The edge scratch lives in a
+    fixed 32 MiB array inside the library, so N is limited to
+    SWEPT_NOALLOC_MAX_N and concurrent calls on different streams race.
+    """
+    prm = (ctypes.c_double * len(params))(*[float(x) for x in params])
+    _check(load().swept_advance_noalloc(int(N), int(stencil_id), prm, len(params), int(dtype), int(B),
+                                        _dev_ptr(u, 8 * int(N), "u"), int(nsteps), _stream(stream)),
+           "swept_advance_noalloc")
+    return u

@@ -90,6 +90,7 @@ const char* swept_strerror(int code) {
     case SWEPT_ECUDA: return "CUDA error";
     case SWEPT_ETIMEOUT: return "device-side wait timed out";
     case SWEPT_ENOTSUP: return "not supported by this build";
+    case SWEPT_ETOOBIG: return "problem exceeds the fixed scratch of swept_advance_noalloc";
     default: return "unknown status";
   }
 }
