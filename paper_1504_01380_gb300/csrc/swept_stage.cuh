@@ -18,20 +18,24 @@
 //   computable on [r m, B - r m), the shrinking triangle.  After level m is
 //   computed its leading edges are kept: the 2r left-most values
 //   [r m, r m + 2r) and the 2r right-most values [B - r m - 2r, B - r m), for
-//   m = 0..ht-1 (Section 3: "two left-most outputs of every sub-timestep"
-//   for a 3-point stencil).  With ht = h the top level is 2r points wide.
+//   m = 0..ht-1 (Section 3: with a 3-point stencil a node sends its two
+//   outermost values of each level).  With ht = h the top level is 2r points wide.
 //
 // Every lane computes all its K points at every level; points outside the
 // computable interval get values that nothing reads later (they are either
 // overwritten by a placement or never read again).  Placements and captures
-// happen at compile-time register offsets: levels are processed in phases
-// of K/r levels, during which the interval boundary stays in one lane and
-// moves r registers per level.
+// happen at compile-time register offsets: level m = P*(K/r) + j has its
+// boundary in lane P (or its mirror) at register r*j + const, so the code for
+// the K/r possible j is generated once each and selected by a uniform branch
+// tree of depth log2(K/r); the level computation itself is emitted once (an
+// unrolled phase of K/r levels overflows the instruction cache for K >= 16).
 //
 // Layout of one window's edges in global memory (elements of type E):
 //   [ L[0][0..2r) L[1][..] ... L[h-1][..] | R[0][0..2r) ... R[h-1][..] ]
 // i.e. 2B elements per window, window w at offset w*2B.
 #pragma once
+
+#include <type_traits>
 
 #include "swept_internal.h"
 
@@ -47,35 +51,73 @@ struct StageImpl {
   static constexpr int L = K / R;      // levels per phase
   static_assert(K % R == 0, "K must be a multiple of the stencil radius");
 
+  // Placement for V-fill level mp = P*L + J: left arm at positions
+  // 16K - R*mp - 2R + q, right arm at 16K + R*mp + q (level mp values).
+  template <int J>
+  static __device__ __forceinline__ void place(Tile<DT, K>& t, const E* sL, const E* sR, int mp, int P,
+                                               int lane) {
+#pragma unroll
+    for (int q = 0; q < 2 * R; ++q) {
+      const int cc = K - R * J - 2 * R + q;
+      const int dl = cc < 0 ? 1 : 0;
+      const int k = cc < 0 ? cc + K : cc;
+      const E v = sL[mp * 2 * R + q];
+      if (lane == 15 - P - dl) t.put(k, v);
+    }
+#pragma unroll
+    for (int q = 0; q < 2 * R; ++q) {
+      const int cc = R * J + q;
+      const int dr = cc >= K ? 1 : 0;
+      const int k = cc - dr * K;
+      const E v = sR[mp * 2 * R + q];
+      if (lane == 16 + P + dr) t.put(k, v);
+    }
+  }
+
+  // Capture for trapezoid level m = P*L + J: left edge at positions
+  // P*K + R*J + q, right edge at (31 - P)*K + K - R*J - 2R + q.
+  template <int J>
+  static __device__ __forceinline__ void capture(const Tile<DT, K>& t, E* oL, E* oR, int m, int P,
+                                                 int lane) {
+#pragma unroll
+    for (int q = 0; q < 2 * R; ++q) {
+      const int cc = R * J + q;
+      const int dl = cc >= K ? 1 : 0;
+      const int k = cc - dl * K;
+      if (lane == P + dl) oL[m * 2 * R + q] = t.get(k);
+    }
+#pragma unroll
+    for (int q = 0; q < 2 * R; ++q) {
+      const int cc = K - R * J - 2 * R + q;
+      const int dr = cc < 0 ? 1 : 0;
+      const int k = cc + dr * K;
+      if (lane == 31 - P - dr) oR[m * 2 * R + q] = t.get(k);
+    }
+  }
+
+  // Calls f(integral_constant<int, j>) for the runtime j in [LO, HI), with a
+  // uniform branch tree.
+  template <int LO, int HI, class F>
+  static __device__ __forceinline__ void select(int j, F&& f) {
+    if constexpr (HI - LO == 1) {
+      f(std::integral_constant<int, LO>{});
+    } else {
+      constexpr int MID = (LO + HI) / 2;
+      if (j < MID) select<LO, MID>(j, f);
+      else select<MID, HI>(j, f);
+    }
+  }
+
   // Levels 1..hv of the V-fill; sL / sR hold the arms (level-major, 2r each).
   static __device__ __forceinline__ void vfill(Tile<DT, K>& t, const E* sL, const E* sR, int hv,
                                                int lane, const Consts& c) {
     const int hmain = hv < H ? hv : H - 1;
-    for (int P = 0; P * L < hmain; ++P) {
-#pragma unroll
-      for (int j = 0; j < L; ++j) {
-        const int mp = P * L + j;            // level mp values are placed, mp+1 computed
-        if (mp >= hmain) break;
-        // left arm, positions 16K - R*mp - 2R + q
-#pragma unroll
-        for (int q = 0; q < 2 * R; ++q) {
-          const int cc = K - R * j - 2 * R + q;
-          const int dl = cc < 0 ? 1 : 0;
-          const int k = cc < 0 ? cc + K : cc;
-          const E v = sL[mp * 2 * R + q];
-          if (lane == 15 - P - dl) t.put(k, v);
-        }
-        // right arm, positions 16K + R*mp + q
-#pragma unroll
-        for (int q = 0; q < 2 * R; ++q) {
-          const int cc = R * j + q;
-          const int dr = cc >= K ? 1 : 0;
-          const int k = cc - dr * K;
-          const E v = sR[mp * 2 * R + q];
-          if (lane == 16 + P + dr) t.put(k, v);
-        }
-        tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr);
-      }
+#pragma unroll 1
+    for (int mp = 0; mp < hmain; ++mp) {          // level mp values placed, mp+1 computed
+      const int P = mp / L;
+      const int j = mp - P * L;
+      select<0, L>(j, [&](auto J) { place<decltype(J)::value>(t, sL, sR, mp, P, lane); });
+      tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr);
     }
     if (hv == H) {
       // Last level: the arms reach r points beyond the window on each side.
@@ -101,29 +143,12 @@ struct StageImpl {
   // top level when ht < h).
   static __device__ __forceinline__ void trapezoid(Tile<DT, K>& t, E* oL, E* oR, int ht, int lane,
                                                    const Consts& c) {
-    for (int P = 0; P * L < ht; ++P) {
-#pragma unroll
-      for (int j = 0; j < L; ++j) {
-        const int m = P * L + j;
-        if (m >= ht) break;
-        if (m > 0) tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr);
-        // left edge: positions P*K + R*j + q
-#pragma unroll
-        for (int q = 0; q < 2 * R; ++q) {
-          const int cc = R * j + q;
-          const int dl = cc >= K ? 1 : 0;
-          const int k = cc - dl * K;
-          if (lane == P + dl) oL[m * 2 * R + q] = t.get(k);
-        }
-        // right edge: positions (31 - P)*K + K - R*j - 2R + q
-#pragma unroll
-        for (int q = 0; q < 2 * R; ++q) {
-          const int cc = K - R * j - 2 * R + q;
-          const int dr = cc < 0 ? 1 : 0;
-          const int k = cc + dr * K;
-          if (lane == 31 - P - dr) oR[m * 2 * R + q] = t.get(k);
-        }
-      }
+#pragma unroll 1
+    for (int m = 0; m < ht; ++m) {
+      if (m > 0) tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr);
+      const int P = m / L;
+      const int j = m - P * L;
+      select<0, L>(j, [&](auto J) { capture<decltype(J)::value>(t, oL, oR, m, P, lane); });
     }
   }
 
