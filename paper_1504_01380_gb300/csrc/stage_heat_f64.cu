@@ -1,8 +1,12 @@
 // Instantiation of the swept stage kernel: heat, f64.
+#include "swept_ring.cuh"
 #include "swept_stage.cuh"
 
 namespace swept {
 cudaError_t launch_stage_heat_f64(int K, const StageArgs& a, cudaStream_t s) {
   return launch_stage_dispatch<kHeat, F64>(K, a, s);
+}
+cudaError_t launch_ring_heat_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s) {
+  return launch_ring_dispatch<kHeat, F64>(K, a, nwarps, s);
 }
 }  // namespace swept

@@ -1,0 +1,217 @@
+// Ring-pipelined diamond stage (Section 3's diamonds, computed two at a time).
+//
+// The per-window stage kernel leaves half of its lanes idle: a diamond is a
+// V-fill whose computable gap grows by r points per side per level and then a
+// triangle that shrinks by r per side, inside a rectangle of B points by 2h
+// levels.  Here one warp streams a run of consecutive windows of one stage and
+// overlaps the V-fill of window w+1 with the triangle of window w: at level m
+// the fill covers 2rm points and the triangle B - 2rm, so together they keep
+// every lane busy.
+//
+// Layout: a register ring of M = 32*S slots, S = K + r per lane, lanes in a
+// ring (lane 31's right neighbour is lane 0).  The window being filled sits
+// at ring offset c (0 or M/2), the window being emptied at c + M/2; the two
+// regions are separated by two gaps of 16r slots.  Each level:
+//   1. the triangle's leading edges of the previous level (2r values on each
+//      side, adjacent to the gaps) are captured to shared memory;
+//   2. the V's arm values of the previous level (2r per side, read from the
+//      previous stage's edges) are placed into the gaps, where the fill's
+//      boundary points read them;
+//   3. all M slots are advanced one level.
+// After h levels the filled window is flat and becomes the window being
+// emptied in the next slot (same offset), and the next window is filled at
+// the other offset.  A run of n windows takes n + 1 slots; the first slot
+// only fills and the last only empties.
+//
+// Every boundary position is r*(level) plus a constant, so with levels in
+// phases of S/r the boundary stays in one lane and moves r registers per
+// level; the register offsets are compile-time, selected by a uniform branch
+// tree as in the per-window kernel.  The values computed are exactly those
+// of the per-window kernel (same expression per point, only the order of
+// independent updates changes), so results are bit-identical.
+#pragma once
+
+#include <type_traits>
+
+#include "swept_internal.h"
+
+namespace swept {
+
+template <int ST, class DT, int K>
+struct RingImpl {
+  using E = typename DT::E;
+  using C = typename DT::C;
+  static constexpr int R = Radius<ST>::value;
+  static constexpr int B = 32 * K;          // window width
+  static constexpr int S = K + R;           // ring slots per lane
+  static constexpr int H = B / (2 * R);     // levels per slot
+  static constexpr int L = S / R;           // levels per phase
+  static_assert(K % R == 0, "K must be a multiple of the stencil radius");
+
+  // Compile-time parts of the four boundary positions for phase step J.
+  //   shrink left edge : p = c + M/2 + R*mp + q           = c + XSL + P*S
+  //   shrink right edge: p = c + M/2 + B - R*mp - 2R + q  = c + XSR - P*S
+  //   fill left arm    : p = c + B/2 - R*mp - 2R + q      = c + XGL - P*S
+  //   fill right arm   : p = c + B/2 + R*mp + q           = c + XGR + P*S
+  // with R*mp = P*S + R*J and M/2 = 16S, B = 32K.
+  template <int J, int Q> struct Pos {
+    static constexpr int XSL = R * J + Q + 16 * S;
+    static constexpr int XSR = 48 * S - 34 * R - R * J + Q;
+    static constexpr int XGL = 16 * S - 18 * R - R * J + Q;
+    static constexpr int XGR = 16 * S - 16 * R + R * J + Q;
+  };
+
+  template <int J, int Q>
+  static __device__ __forceinline__ void capture_q(const Tile<DT, S>& t, E* sOL, E* sOR, int mp, int P,
+                                                   int cl, int lane) {
+    using Ps = Pos<J, Q>;
+    if (lane == ((cl + Ps::XSL / S + P) & 31)) sOL[mp * 2 * R + Q] = t.get(Ps::XSL % S);
+    if (lane == ((cl + Ps::XSR / S - P) & 31)) sOR[mp * 2 * R + Q] = t.get(Ps::XSR % S);
+  }
+  template <int J, int Q>
+  static __device__ __forceinline__ void place_q(Tile<DT, S>& t, const E (&al)[2 * R], const E (&ar)[2 * R],
+                                                 int P, int cl, int lane) {
+    using Ps = Pos<J, Q>;
+    if (lane == ((cl + Ps::XGL / S - P) & 31)) t.put(Ps::XGL % S, al[Q]);
+    if (lane == ((cl + Ps::XGR / S + P) & 31)) t.put(Ps::XGR % S, ar[Q]);
+  }
+  template <int J, int... Qs>
+  static __device__ __forceinline__ void capture_all(const Tile<DT, S>& t, E* sOL, E* sOR, int mp, int P,
+                                                     int cl, int lane, std::integer_sequence<int, Qs...>) {
+    (capture_q<J, Qs>(t, sOL, sOR, mp, P, cl, lane), ...);
+  }
+  template <int J, int... Qs>
+  static __device__ __forceinline__ void place_all(Tile<DT, S>& t, const E (&al)[2 * R], const E (&ar)[2 * R],
+                                                   int P, int cl, int lane, std::integer_sequence<int, Qs...>) {
+    (place_q<J, Qs>(t, al, ar, P, cl, lane), ...);
+  }
+
+  template <int LO, int HI, class F>
+  static __device__ __forceinline__ void select(int j, F&& f) {
+    if constexpr (HI - LO == 1) {
+      f(std::integral_constant<int, LO>{});
+    } else {
+      constexpr int MID = (LO + HI) / 2;
+      if (j < MID) select<LO, MID>(j, f);
+      else select<MID, HI>(j, f);
+    }
+  }
+
+  static __device__ __forceinline__ void warp_copy(E* __restrict__ dst, const E* __restrict__ src, int n,
+                                                   int lane) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (int i = lane; i < n / 2; i += 32) d4[i] = s4[i];
+  }
+
+  // One warp: windows [w0, w1) of a full diamond stage (hv = ht = h).
+  static __device__ void run(const StageArgs& a, E* sm, int w0, int w1) {
+    const int lane = threadIdx.x & 31;
+    const E* ein = static_cast<const E*>(a.ein);
+    E* eout = static_cast<E*>(a.eout);
+    // sm[0, B): fill's left arm in, then the emptied window's left edges out;
+    // sm[B, 2B): fill's right arm in, then right edges out.
+    E* s0 = sm;
+    E* s1 = sm + B;
+    Tile<DT, S> t;
+    t.zero();
+    const int nrun = w1 - w0;
+    for (int slot = 0; slot <= nrun; ++slot) {
+      const bool fill = slot < nrun;
+      const bool empty = slot > 0;
+      const int cl = (slot & 1) ? 16 : 0;          // ring offset of the filled window, in lanes
+      if (fill) {
+        const int w = w0 + slot;
+        const int wl = a.offset ? w : (w == 0 ? a.nwin - 1 : w - 1);
+        const int wr = a.offset ? (w + 1 == a.nwin ? 0 : w + 1) : w;
+        warp_copy(s0, ein + (int64_t)wl * (2 * B) + B, B, lane);
+        warp_copy(s1, ein + (int64_t)wr * (2 * B), B, lane);
+      }
+      __syncwarp();
+      int P = 0, j = 0;
+#pragma unroll 1
+      for (int mp = 0; mp < H; ++mp) {
+        E al[2 * R], ar[2 * R];
+#pragma unroll
+        for (int q = 0; q < 2 * R; ++q) {
+          al[q] = s0[mp * 2 * R + q];
+          ar[q] = s1[mp * 2 * R + q];
+        }
+        __syncwarp();
+        // (the emptied window sits at offset cl + M/2: the XS* constants include M/2)
+        select<0, L>(j, [&](auto JJ) {
+          constexpr int J = decltype(JJ)::value;
+          if (empty) capture_all<J>(t, s0, s1, mp, P, cl, lane, std::make_integer_sequence<int, 2 * R>{});
+          if (fill) place_all<J>(t, al, ar, P, cl, lane, std::make_integer_sequence<int, 2 * R>{});
+        });
+        tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr);
+        if (++j == L) { j = 0; ++P; }
+      }
+      __syncwarp();
+      if (empty) {
+        const int ws = w0 + slot - 1;
+        warp_copy(eout + (int64_t)ws * (2 * B), s0, B, lane);
+        warp_copy(eout + (int64_t)ws * (2 * B) + B, s1, B, lane);
+      }
+      __syncwarp();
+    }
+  }
+};
+
+template <int ST, class DT, int K>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+swept_ring_kernel(const StageArgs a, int nwarps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using E = typename DT::E;
+  constexpr int B = 32 * K;
+  E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * B);
+  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (gw >= nwarps) return;
+  // balanced contiguous runs: warp gw takes [gw*n/W, (gw+1)*n/W)
+  const int w0 = (int)(((int64_t)gw * a.nwin) / nwarps);
+  const int w1 = (int)(((int64_t)(gw + 1) * a.nwin) / nwarps);
+  if (w1 > w0) RingImpl<ST, DT, K>::run(a, sm, w0, w1);
+}
+
+// Launch with `nwarps` warps; 0 picks min(resident warp slots of the GPU,
+// nwin / 2), so that every warp streams at least two windows when it can.
+template <int ST, class DT, int K>
+cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
+  constexpr int B = 32 * K;
+  const size_t smem = stage_smem_bytes(B);
+  cudaError_t e = cudaFuncSetAttribute(swept_ring_kernel<ST, DT, K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (nwarps <= 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, swept_ring_kernel<ST, DT, K>,
+                                                      kWarpsPerBlock * 32, smem);
+    if (e != cudaSuccess) return e;
+    nwarps = sms * (per_sm > 0 ? per_sm : 1) * kWarpsPerBlock;
+    if (nwarps > a.nwin / 2) nwarps = a.nwin / 2;
+    if (nwarps < 1) nwarps = 1;
+  }
+  if (nwarps > a.nwin) nwarps = a.nwin;
+  const int grid = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  swept_ring_kernel<ST, DT, K><<<grid, kWarpsPerBlock * 32, smem, s>>>(a, nwarps);
+  return cudaGetLastError();
+}
+
+template <int ST, class DT>
+cudaError_t launch_ring_dispatch(int K, const StageArgs& a, int nwarps, cudaStream_t s) {
+  switch (K) {
+    case 1:
+      if constexpr (Radius<ST>::value == 1) return launch_ring_k<ST, DT, 1>(a, nwarps, s);
+      else return cudaErrorInvalidValue;
+    case 2: return launch_ring_k<ST, DT, 2>(a, nwarps, s);
+    case 4: return launch_ring_k<ST, DT, 4>(a, nwarps, s);
+    case 8: return launch_ring_k<ST, DT, 8>(a, nwarps, s);
+    case 16: return launch_ring_k<ST, DT, 16>(a, nwarps, s);
+    case 32: return launch_ring_k<ST, DT, 32>(a, nwarps, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace swept
