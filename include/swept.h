@@ -93,6 +93,25 @@ void swept_destroy(swept_plan_t plan);
 /* Query: B, h = B/(2 radius), N, dtype, stencil, radius in info[0..6). */
 int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
 
+/*
+ * swept_plan_set -- tuning options of a plan (used by the autotuner and the
+ * tests; results do not depend on them, only speed does).
+ *   SWEPT_OPT_DIAMOND    kernel for full diamond stages:
+ *                        SWEPT_DIAMOND_AUTO (default), SWEPT_DIAMOND_WINDOW
+ *                        (one warp per window), SWEPT_DIAMOND_RING (one warp
+ *                        streams a run of windows, overlapping the V-fill of
+ *                        one with the triangle of the previous).
+ *   SWEPT_OPT_RING_WARPS warps of a ring launch; 0 = min(resident warp slots,
+ *                        N/B/2).
+ * Errors: SWEPT_EINVAL for an unknown option or value.
+ */
+#define SWEPT_OPT_DIAMOND     0
+#define SWEPT_OPT_RING_WARPS  1
+#define SWEPT_DIAMOND_AUTO    0
+#define SWEPT_DIAMOND_WINDOW  1
+#define SWEPT_DIAMOND_RING    2
+int swept_plan_set(swept_plan_t plan, int option, int64_t value);
+
 /* ---- advance ---------------------------------------------------------- */
 
 /*
@@ -104,7 +123,8 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  * the V of leading edges that the two neighbouring triangles wrote to the
  * plan's edge buffer.  nsteps = q*h + rem (h = B/(2 radius)) takes q + 1
  * launches when rem == 0, q + 2 otherwise (the last stage ends with a
- * trapezoid of height rem and its fill).
+ * trapezoid of height rem and its fill).  Full diamond stages run on the
+ * kernel chosen by SWEPT_OPT_DIAMOND.
  *   u       device, state layout of the plan's dtype, overwritten in place.
  *   nsteps  >= 0; 0 is a no-op.
  * Errors: SWEPT_EINVAL (null plan/u, nsteps < 0), SWEPT_ECUDA.
@@ -118,6 +138,30 @@ int swept_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream);
  * as the second buffer.  Same arguments and errors as swept_advance.
  */
 int swept_naive_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream);
+
+/* ---- adjoint ----------------------------------------------------------- */
+
+/*
+ * swept_adjoint -- vector-Jacobian product of the nsteps-step map:
+ * grad_u0 = (d u(nsteps) / d u0)^T lambda_T.  With lambda_T = u(nsteps) this
+ * is the gradient of J = 1/2 sum u(nsteps)^2 with respect to u0.  The paper
+ * has no adjoint; the transposed step is derived from the update's Jacobian:
+ *   heat: lambda' = lambda + r L2 lambda (the forward update itself);
+ *   KS:   lambda'_j = lambda_j + 2a u_j (lambda_{j-1} - lambda_{j+1})
+ *                     + b (L2 lambda)_j + e (L2 L2 lambda)_j,
+ * u_j the forward state at that level.  The cotangent is advanced backwards
+ * in time by the swept rule (same stages, transposed stencil).  KS needs the
+ * forward state at every level: the forward pass keeps a checkpoint of u
+ * every 2*K_cycles*h levels (K_cycles swept cycles of two stages; <= 0 means
+ * 64), and each segment is recomputed from its checkpoint into a tape that
+ * the reverse sweep reads.  FP64 plans only.
+ *   u0, lambda_T, grad_u0  device double[N]; grad_u0 may not alias u0.
+ * Scratch (plan-owned, grown on demand): (1 + segments + 2*K_cycles*h) * 8N
+ * bytes for KS; none for heat.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP (F32C plan), SWEPT_ENOMEM, SWEPT_ECUDA.
+ */
+int swept_adjoint(swept_plan_t plan, const void *u0, const void *lambda_T, void *grad_u0,
+                  int64_t nsteps, int K_cycles, void *stream);
 
 /* ---- FP32-compensated state conversion -------------------------------- */
 
@@ -145,6 +189,76 @@ int swept_f32c_merge(int64_t N, const void *u32c, double *u64, void *stream);
  */
 int swept_reduce(swept_plan_t plan, const void *u, int what, const void *v,
                  double *out, void *stream);
+
+/* ---- batched persistent launch ----------------------------------------- */
+
+/* One problem of a batch.  Its state (layout of the batch's dtype, 8N bytes)
+ * lives at byte `offset` of the caller's pool; offset must be 16-byte
+ * aligned.  params: heat {r, unused}; KS {dt, dx}. */
+typedef struct {
+  int64_t N;
+  int64_t nsteps;
+  int64_t offset;
+  int stencil;
+  int reserved;
+  double params[2];
+} swept_problem_t;
+
+typedef struct swept_batch_s *swept_batch_t;
+
+/*
+ * swept_batch_plan -- plan one persistent launch that advances `nprob`
+ * independent periodic problems of uneven N and nsteps (each as
+ * swept_advance would; Section 3's stages, per problem).
+ *   probs   host array, copied.  Each N must be a multiple of the tile width
+ *           of its stencil.
+ *   dtype   SWEPT_F64 or SWEPT_F32C for the whole batch.
+ *   B_heat, B_ks  tile widths for heat and KS problems, each 256 or 512
+ *           (0 = 512); picked by the autotuner in the Python layer.
+ * The work is one queue of (problem, window, stage) items in stage-major
+ * order; a warp takes an item, waits (bounded) until the two windows of the
+ * previous stage it reads from have published their edges, runs the stage
+ * on its window and publishes.  Allocates per-problem edge buffers (32N
+ * bytes each), per-window stage counters and the item tables.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP, SWEPT_ENOMEM, SWEPT_ECUDA.
+ */
+int swept_batch_plan(swept_batch_t *out, int nprob, const swept_problem_t *probs, int dtype,
+                     int B_heat, int B_ks);
+
+/*
+ * swept_batch_set -- options.
+ *   SWEPT_BOPT_TIMEOUT_S  budget of every device-side wait, seconds (default
+ *                         2): a wait that runs out records SWEPT_ETIMEOUT
+ *                         and the launch winds down instead of hanging.
+ *   SWEPT_BOPT_DROP_ITEM  test hook (a message lost on the host side): the
+ *                         item with this queue index never publishes its
+ *                         counter, so the items waiting on it time out.
+ *                         -1 = none (default).
+ *   SWEPT_BOPT_GRID       number of thread blocks (default: all resident).
+ */
+#define SWEPT_BOPT_TIMEOUT_S  0
+#define SWEPT_BOPT_DROP_ITEM  1
+#define SWEPT_BOPT_GRID       2
+int swept_batch_set(swept_batch_t batch, int option, double value);
+
+/* Query: items, stages, windows, grid, problems in info[0..5). */
+int swept_batch_info(swept_batch_t batch, int64_t *info, int ninfo);
+
+/*
+ * swept_advance_batch -- advance every problem of the batch in `pool`
+ * (device) in place, as one CUDA graph (counter/status/flag resets + one
+ * persistent kernel) captured on first use for this pool pointer and
+ * replayed afterwards.  Asynchronous; errors found on the device are read
+ * with swept_batch_status.
+ * Errors: SWEPT_EINVAL, SWEPT_ECUDA.
+ */
+int swept_advance_batch(swept_batch_t batch, void *pool, void *stream);
+
+/* Synchronise `stream` and return the device status of the last advance:
+ * SWEPT_OK or SWEPT_ETIMEOUT. */
+int swept_batch_status(swept_batch_t batch, void *stream);
+
+void swept_batch_destroy(swept_batch_t batch);
 
 /* ---- advance without any device allocation ---------------------------- */
 

@@ -21,6 +21,8 @@ SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT = 0, 1, 2
 SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP = 0, -1, -2, -3, -4, -5
 SWEPT_ETOOBIG = -6
 SWEPT_NOALLOC_MAX_N = 1 << 20
+SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS = 0, 1
+SWEPT_DIAMOND_AUTO, SWEPT_DIAMOND_WINDOW, SWEPT_DIAMOND_RING = 0, 1, 2
 
 RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2}
 
@@ -28,8 +30,18 @@ RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2}
 EXPORTS = (
     "swept_plan", "swept_destroy", "swept_plan_info", "swept_advance", "swept_naive_advance",
     "swept_f32c_split", "swept_f32c_merge", "swept_reduce", "swept_strerror", "swept_version",
-    "swept_advance_noalloc",
+    "swept_advance_noalloc", "swept_plan_set",
+    "swept_batch_plan", "swept_batch_set", "swept_batch_info", "swept_advance_batch",
+    "swept_batch_status", "swept_batch_destroy", "swept_adjoint",
 )
+
+SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID = 0, 1, 2
+
+
+class swept_problem_t(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("nsteps", ctypes.c_int64), ("offset", ctypes.c_int64),
+                ("stencil", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("params", ctypes.c_double * 2)]
 
 _lock = threading.Lock()
 _lib = None
@@ -60,6 +72,8 @@ def load(path: str | None = None):
         L.swept_destroy.restype = None
         L.swept_plan_info.argtypes = [vp, ctypes.POINTER(i64), i32]
         L.swept_plan_info.restype = i32
+        L.swept_plan_set.argtypes = [vp, i32, i64]
+        L.swept_plan_set.restype = i32
         for f in ("swept_advance", "swept_naive_advance"):
             getattr(L, f).argtypes = [vp, vp, i64, vp]
             getattr(L, f).restype = i32
@@ -72,6 +86,20 @@ def load(path: str | None = None):
         L.swept_advance_noalloc.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_double), i32, i32, i32,
                                             vp, i64, vp]
         L.swept_advance_noalloc.restype = i32
+        L.swept_batch_plan.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(swept_problem_t), i32, i32, i32]
+        L.swept_batch_plan.restype = i32
+        L.swept_batch_set.argtypes = [vp, i32, ctypes.c_double]
+        L.swept_batch_set.restype = i32
+        L.swept_batch_info.argtypes = [vp, ctypes.POINTER(i64), i32]
+        L.swept_batch_info.restype = i32
+        L.swept_advance_batch.argtypes = [vp, vp, vp]
+        L.swept_advance_batch.restype = i32
+        L.swept_batch_status.argtypes = [vp, vp]
+        L.swept_batch_status.restype = i32
+        L.swept_batch_destroy.argtypes = [vp]
+        L.swept_batch_destroy.restype = None
+        L.swept_adjoint.argtypes = [vp, vp, vp, vp, i64, i32, vp]
+        L.swept_adjoint.restype = i32
         L.swept_strerror.argtypes = [i32]
         L.swept_strerror.restype = ctypes.c_char_p
         L.swept_version.argtypes = []
@@ -153,6 +181,12 @@ def swept_plan(N: int, radius: int, stencil_id: int, params, dtype: int, B: int 
     return Plan(h, int(N), int(stencil_id), int(dtype), int(info[0]), int(info[1]), params)
 
 
+def swept_plan_set(plan: Plan, option: int, value: int) -> Plan:
+    """Set a tuning option (SWEPT_OPT_*) of the plan; results do not depend on it."""
+    _check(load().swept_plan_set(plan.handle, int(option), int(value)), "swept_plan_set")
+    return plan
+
+
 def swept_advance(plan: Plan, u, nsteps: int, stream=None):
     """u <- u after nsteps sub-timesteps (swept rule), in place on ``stream``."""
     _check(load().swept_advance(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(nsteps),
@@ -217,3 +251,117 @@ def swept_advance_noalloc(N: int, stencil_id: int, params, dtype: int, B: int, u
                                         _dev_ptr(u, 8 * int(N), "u"), int(nsteps), _stream(stream)),
            "swept_advance_noalloc")
     return u
+
+
+class Batch:
+    """A planned batch (``swept_batch_plan`` / ``swept_batch_destroy``).
+
+    ``offsets[i]`` is the byte offset of problem i's state in the pool and
+    ``pool_bytes`` the pool size, both chosen by ``swept_batch_plan`` when
+    the caller does not give offsets.
+    """
+
+    def __init__(self, handle, offsets, pool_bytes, sizes, dtype):
+        self._h = handle
+        self.offsets, self.pool_bytes, self.sizes, self.dtype = offsets, pool_bytes, sizes, dtype
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("batch was destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        v = (ctypes.c_int64 * 5)()
+        _check(load().swept_batch_info(self.handle, v, 5), "swept_batch_info")
+        return {"items": v[0], "stages": v[1], "windows": v[2], "grid": v[3], "problems": v[4]}
+
+    def destroy(self):
+        if self._h is not None:
+            load().swept_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def swept_batch_plan(problems, dtype: int, B_heat: int = 0, B_ks: int = 0, offsets=None) -> Batch:
+    """problems: iterable of (stencil, N, nsteps, params).  Offsets default to a packed pool."""
+    problems = list(problems)
+    arr = (swept_problem_t * len(problems))()
+    offs, pos = [], 0
+    for i, (stencil, n, nsteps, params) in enumerate(problems):
+        off = offsets[i] if offsets is not None else pos
+        pos = max(pos, off + 8 * int(n))
+        pos = (pos + 255) // 256 * 256
+        prm = list(params) + [0.0] * (2 - len(params))
+        arr[i] = swept_problem_t(int(n), int(nsteps), int(off), int(stencil), 0,
+                                 (ctypes.c_double * 2)(*prm))
+        offs.append(int(off))
+    h = ctypes.c_void_p()
+    _check(load().swept_batch_plan(ctypes.byref(h), len(problems), arr, int(dtype), int(B_heat), int(B_ks)),
+           "swept_batch_plan")
+    return Batch(h, offs, pos, [int(p[1]) for p in problems], int(dtype))
+
+
+def swept_batch_set(batch: Batch, option: int, value: float) -> Batch:
+    _check(load().swept_batch_set(batch.handle, int(option), float(value)), "swept_batch_set")
+    return batch
+
+
+def swept_advance_batch(batch: Batch, pool, stream=None):
+    """Advance every problem of the batch in ``pool`` (a CUDA tensor of pool_bytes bytes)."""
+    _check(load().swept_advance_batch(batch.handle, _dev_ptr(pool, batch.pool_bytes, "pool"),
+                                      _stream(stream)), "swept_advance_batch")
+    return pool
+
+
+def swept_batch_status(batch: Batch, stream=None) -> int:
+    """Synchronise and return the device status of the last advance (0 or SWEPT_ETIMEOUT)."""
+    return int(load().swept_batch_status(batch.handle, _stream(stream)))
+
+
+def swept_adjoint(plan: Plan, u0, lam_T, nsteps: int, K_cycles: int = 64, out=None, stream=None):
+    """(d u(nsteps)/d u0)^T lam_T for an FP64 plan; lam_T = u(nsteps) gives grad of 1/2 sum u^2."""
+    import torch
+    if out is None:
+        out = torch.empty_like(u0)
+    _check(load().swept_adjoint(plan.handle, _dev_ptr(u0, plan.state_bytes, "u0"),
+                                _dev_ptr(lam_T, plan.state_bytes, "lam_T"),
+                                _dev_ptr(out, plan.state_bytes, "grad"), int(nsteps), int(K_cycles),
+                                _stream(stream)), "swept_adjoint")
+    return out
+
+
+def _make_autograd():
+    import torch
+
+    class SweptAdvance(torch.autograd.Function):
+        """u(nsteps) = swept advance of u0; backward runs the swept adjoint."""
+
+        @staticmethod
+        def forward(ctx, u0, plan, nsteps, K_cycles=64):
+            u = u0.detach().clone().contiguous()
+            swept_advance(plan, u, nsteps)
+            ctx.save_for_backward(u0.detach().contiguous())
+            ctx.plan, ctx.nsteps, ctx.K = plan, int(nsteps), int(K_cycles)
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (u0,) = ctx.saved_tensors
+            g = swept_adjoint(ctx.plan, u0, grad_out.contiguous(), ctx.nsteps, ctx.K)
+            return g, None, None, None
+
+    return SweptAdvance
+
+
+def __getattr__(name):
+    if name == "SweptAdvance":
+        cls = _make_autograd()
+        globals()["SweptAdvance"] = cls
+        return cls
+    raise AttributeError(name)

@@ -22,6 +22,10 @@ struct swept_plan_s {
   unsigned char* edges;   // two buffers of nwin * 2B elements of 8 bytes
   size_t edge_half;       // bytes per buffer
   double* red;            // 2 * kReduceBlocks partials
+  int diamond;            // SWEPT_DIAMOND_*
+  int ring_warps;         // 0 = automatic
+  double* adj;            // adjoint scratch: work state, checkpoints, tape
+  size_t adj_bytes;
 };
 
 namespace {
@@ -66,6 +70,22 @@ cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t
                                  : swept::launch_stage_heat_f32c(p->K, a, s);
   return p->dtype == SWEPT_F64 ? swept::launch_stage_ks_f64(p->K, a, s)
                                : swept::launch_stage_ks_f32c(p->K, a, s);
+}
+
+cudaError_t launch_ring(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
+  if (p->stencil == SWEPT_HEAT)
+    return p->dtype == SWEPT_F64 ? swept::launch_ring_heat_f64(p->K, a, p->ring_warps, s)
+                                 : swept::launch_ring_heat_f32c(p->K, a, p->ring_warps, s);
+  return p->dtype == SWEPT_F64 ? swept::launch_ring_ks_f64(p->K, a, p->ring_warps, s)
+                               : swept::launch_ring_ks_f32c(p->K, a, p->ring_warps, s);
+}
+
+// The ring kernel needs at least two windows per warp to gain over the
+// per-window kernel; automatic choice: ring from 8 windows up.
+bool use_ring(const swept_plan_s* p) {
+  if (p->diamond == SWEPT_DIAMOND_RING) return true;
+  if (p->diamond == SWEPT_DIAMOND_WINDOW) return false;
+  return p->nwin >= 8;
 }
 
 // Default tile width: the largest of 512, 256, ... that divides N and keeps
@@ -149,6 +169,7 @@ void swept_destroy(swept_plan_t p) {
   cudaDeviceSynchronize();
   if (p->edges) cudaFree(p->edges);
   if (p->red) cudaFree(p->red);
+  if (p->adj) cudaFree(p->adj);
   std::free(p);
 }
 
@@ -159,6 +180,21 @@ int swept_plan_info(swept_plan_t p, int64_t* info, int ninfo) {
   return SWEPT_OK;
 }
 
+int swept_plan_set(swept_plan_t p, int option, int64_t value) {
+  if (!p) return SWEPT_EINVAL;
+  if (option == SWEPT_OPT_DIAMOND) {
+    if (value < SWEPT_DIAMOND_AUTO || value > SWEPT_DIAMOND_RING) return SWEPT_EINVAL;
+    p->diamond = (int)value;
+    return SWEPT_OK;
+  }
+  if (option == SWEPT_OPT_RING_WARPS) {
+    if (value < 0 || value > (int64_t)1 << 30) return SWEPT_EINVAL;
+    p->ring_warps = (int)value;
+    return SWEPT_OK;
+  }
+  return SWEPT_EINVAL;
+}
+
 int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
   if (nsteps == 0) return SWEPT_OK;
@@ -167,19 +203,21 @@ int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   const int64_t q = nsteps / H;
   const int rem = (int)(nsteps % H);
   unsigned char* buf[2] = {p->edges, p->edges + p->edge_half};
-  StageArgs a;
+  StageArgs a{};
   a.u = u;
   a.N = p->N;
   a.nwin = p->nwin;
   a.c = p->c;
   // stage k: windows shifted by B/2 when k is odd (the alternating point
   // sets of Section 3); reads the edges of stage k-1, writes its own.
+  const bool ring = use_ring(p);
   auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
     a.offset = (k & 1) ? p->B / 2 : 0;
     a.hv = hv;
     a.ht = ht;
     a.ein = buf[(k + 1) & 1];
     a.eout = buf[k & 1];
+    if (ring && hv == p->H && ht == p->H) return launch_ring(p, a, s);
     return launch_stage(p, a, s);
   };
   cudaError_t e = cudaSuccess;
@@ -191,6 +229,110 @@ int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     for (int64_t k = 1; k < q && e == cudaSuccess; ++k) e = stage(k, (int)H, (int)H);   // diamonds
     if (e == cudaSuccess) e = stage(q, (int)H, rem);  // last V-fill (+ trapezoid)
     if (e == cudaSuccess && rem > 0) e = stage(q + 1, rem, 0);
+  }
+  return cuda_status(e);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Swept sweep of the adjoint variable lam over `len` levels of the transposed
+// KS step; level tau of the sweep uses the forward state tape[len - tau].
+// Same stage schedule as swept_advance.
+cudaError_t adjoint_sweep(swept_plan_s* p, double* lam, int64_t len, const double* tape, cudaStream_t s) {
+  const int64_t H = p->H;
+  const int64_t q = len / H;
+  const int rem = (int)(len % H);
+  unsigned char* buf[2] = {p->edges, p->edges + p->edge_half};
+  StageArgs a{};
+  a.u = lam;
+  a.N = p->N;
+  a.nwin = p->nwin;
+  a.c = p->c;
+  a.tape = tape;
+  a.tape_len = len;
+  auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
+    a.offset = (k & 1) ? p->B / 2 : 0;
+    a.hv = hv;
+    a.ht = ht;
+    a.ein = buf[(k + 1) & 1];
+    a.eout = buf[k & 1];
+    a.lev_fill = k >= 1 ? (k - 1) * H : 0;
+    a.lev_trap = k * H;
+    return swept::launch_stage_ksadj_f64(p->K, a, s);
+  };
+  cudaError_t e = cudaSuccess;
+  if (q == 0) {
+    e = stage(0, 0, rem);
+    if (e == cudaSuccess) e = stage(1, rem, 0);
+  } else {
+    e = stage(0, 0, (int)H);
+    for (int64_t k = 1; k < q && e == cudaSuccess; ++k) e = stage(k, (int)H, (int)H);
+    if (e == cudaSuccess) e = stage(q, (int)H, rem);
+    if (e == cudaSuccess && rem > 0) e = stage(q + 1, rem, 0);
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad, int64_t nsteps,
+                  int K_cycles, void* stream) {
+  if (!p || !u0 || !lam_T || !grad || nsteps < 0) return SWEPT_EINVAL;
+  if (!aligned16(u0) || !aligned16(lam_T) || !aligned16(grad)) return SWEPT_EINVAL;
+  if (p->dtype != SWEPT_F64) return SWEPT_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)p->N * sizeof(double);
+  cudaError_t e = cudaMemcpyAsync(grad, lam_T, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess || nsteps == 0) return cuda_status(e);
+  if (p->stencil == SWEPT_HEAT) {
+    // dPhi = I + r L2 is symmetric and its transpose applied to lam is the
+    // same update with the same rounding: the adjoint is the forward sweep.
+    return swept_advance(p, grad, nsteps, stream);
+  }
+  if (K_cycles <= 0) K_cycles = 64;
+  int64_t C = 2 * (int64_t)K_cycles * p->H;      // levels per checkpoint segment
+  if (C > nsteps) C = nsteps;
+  const int64_t nseg = (nsteps + C - 1) / C;
+  // scratch: work state (1) + checkpoints (nseg) + tape (C levels)
+  const size_t need = (size_t)(1 + nseg + C) * bytes;
+  if (p->adj_bytes < need) {
+    cudaStreamSynchronize(s);
+    if (p->adj) cudaFree(p->adj);
+    p->adj = nullptr;
+    p->adj_bytes = 0;
+    e = cudaMalloc((void**)&p->adj, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    p->adj_bytes = need;
+  }
+  double* work = p->adj;
+  double* ckpt = work + p->N;
+  double* tape = ckpt + nseg * p->N;
+  // forward pass with a checkpoint at the start of every segment
+  e = cudaMemcpyAsync(work, u0, bytes, cudaMemcpyDeviceToDevice, s);
+  for (int64_t g = 0; g < nseg && e == cudaSuccess; ++g) {
+    e = cudaMemcpyAsync(ckpt + g * p->N, work, bytes, cudaMemcpyDeviceToDevice, s);
+    const int64_t len = (g + 1 < nseg) ? C : nsteps - g * C;
+    if (e == cudaSuccess && g + 1 < nseg) {
+      const int rc = swept_advance(p, work, len, stream);
+      if (rc != SWEPT_OK) return rc;
+    }
+  }
+  // reverse: recompute each segment's trajectory into the tape, then sweep
+  double* lam = static_cast<double*>(grad);
+  for (int64_t g = nseg - 1; g >= 0 && e == cudaSuccess; --g) {
+    const int64_t len = (g + 1 < nseg) ? C : nsteps - g * C;
+    e = cudaMemcpyAsync(tape, ckpt + g * p->N, bytes, cudaMemcpyDeviceToDevice, s);
+    for (int64_t n = 1; n < len && e == cudaSuccess; ++n)
+      e = swept::launch_naive_step(p->stencil, p->dtype, tape + (n - 1) * p->N, tape + n * p->N, p->N,
+                                   p->c, s);
+    if (e == cudaSuccess) e = adjoint_sweep(p, lam, len, tape, s);
   }
   return cuda_status(e);
 }

@@ -1,0 +1,459 @@
+// Batched persistent swept launch: many independent periodic problems of
+// uneven length and step count advanced by one kernel launch.
+//
+// Work items are (problem, window, stage) triples, one swept stage of one
+// window (Section 3's per-node stage), processed by one warp with the same
+// code as the per-window stage kernel.  Items are handed out by one atomic
+// counter in stage-major order over the whole batch: every stage-s item of
+// every problem precedes every stage-(s+1) item.  A stage-s item (s >= 1)
+// reads the leading edges of the two stage-(s-1) windows it straddles, so it
+// waits until both have published: each window has a counter of completed
+// stages, written with release semantics after its edges, and read with
+// acquire semantics.  Items are only waited on by later items and the queue
+// order puts every dependency before its dependant, and warps take items
+// only while running, so the waits always end unless something is lost; as a
+// guard every wait has a clock budget after which the warp records
+// SWEPT_ETIMEOUT in a status word and stops, and the other warps stop taking
+// work once the status is set.  No wait is unbounded.
+//
+// The same wait also protects the edge double buffer from being overwritten
+// early: window w's stage-(s+2) edges go where its stage-s edges were, and
+// the windows that read those (stage s+1, straddling w) are exactly the ones
+// w's stage-(s+2) item waits for.
+//
+// Problems are sorted by stage count (descending) so that the problems still
+// active at stage s are a prefix; an item index decodes to (stage, problem,
+// window) by two binary searches over small tables.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "swept.h"
+#include "swept_internal.h"
+#include "swept_stage.cuh"
+
+namespace swept {
+
+struct BatchProblem {
+  int64_t u_off;          // byte offset of the state in the pool
+  int64_t e_off;          // byte offset of the edge double buffer in the plan's edge pool
+  int64_t f_off;          // index of the first window counter
+  int64_t N;
+  int nwin, B, H, stencil, q, rem, nstages, pad;
+  Consts c;
+};
+
+struct BatchArgs {
+  unsigned char* pool;
+  unsigned char* edges;
+  int* flags;
+  const BatchProblem* probs;    // sorted by nstages, descending
+  const int64_t* cum;           // nprob + 1: windows before problem i (sorted order)
+  const int* nactive;           // per stage: problems still active (a prefix)
+  const int64_t* stage_start;   // nstage_max + 1: first item of each stage
+  int nstage_max;
+  int64_t nitems;
+  unsigned long long* counter;
+  int* status;
+  long long timeout_cycles;
+  int64_t drop_item;            // item whose counter is never published (-1: none)
+};
+
+namespace {
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait until *flag >= target (acquire).  False when the budget ran out.
+__device__ __forceinline__ bool wait_ge(const int* flag, int target, long long t0, long long budget) {
+  for (;;) {
+    if (ld_acquire(flag) >= target) return true;
+    if (clock64() - t0 > budget) return false;
+    __nanosleep(256);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ int upper_index(const T* a, int n, T x) {
+  // largest i in [0, n) with a[i] <= x (a ascending, a[0] <= x)
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__host__ __device__ __forceinline__ void stage_shape(int s, int q, int rem, int H, int& hv, int& ht) {
+  if (q == 0) {
+    hv = s == 0 ? 0 : rem;
+    ht = s == 0 ? rem : 0;
+  } else if (s == 0) {
+    hv = 0; ht = H;
+  } else if (s < q) {
+    hv = H; ht = H;
+  } else if (s == q) {
+    hv = H; ht = rem;
+  } else {
+    hv = rem; ht = 0;
+  }
+}
+
+template <class DT, int KH, int KK>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+swept_batch_kernel(const BatchArgs ba) {
+  using E = typename DT::E;
+  constexpr int BMAX = 32 * (KH > KK ? KH : KK);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * BMAX);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(ba.counter, 1ull);
+    idx = __shfl_sync(kFull, idx, 0);
+    if ((int64_t)idx >= ba.nitems) return;
+    if (ld_acquire(ba.status) != 0) return;
+    const int s = upper_index<int64_t>(ba.stage_start, ba.nstage_max, (int64_t)idx);
+    const int64_t k = (int64_t)idx - ba.stage_start[s];
+    const int i = upper_index<int64_t>(ba.cum, ba.nactive[s], k);
+    const int w = (int)(k - ba.cum[i]);
+    const BatchProblem P = ba.probs[i];
+    StageArgs a;
+    a.u = ba.pool + P.u_off;
+    a.N = P.N;
+    a.nwin = P.nwin;
+    a.offset = (s & 1) ? P.B / 2 : 0;
+    stage_shape(s, P.q, P.rem, P.H, a.hv, a.ht);
+    const int64_t half = (int64_t)P.nwin * 2 * P.B * 8;
+    unsigned char* eb = ba.edges + P.e_off;
+    a.ein = eb + ((s + 1) & 1) * half;
+    a.eout = eb + (s & 1) * half;
+    a.c = P.c;
+    int* flags = ba.flags + P.f_off;
+    if (s > 0) {
+      const int wl = a.offset ? w : (w == 0 ? P.nwin - 1 : w - 1);
+      const int wr = a.offset ? (w + 1 == P.nwin ? 0 : w + 1) : w;
+      const long long t0 = clock64();
+      bool ok = wait_ge(flags + wl, s, t0, ba.timeout_cycles);
+      if (ok) ok = wait_ge(flags + wr, s, t0, ba.timeout_cycles);
+      if (!__all_sync(kFull, ok)) {
+        if (lane == 0) atomicCAS(ba.status, 0, SWEPT_ETIMEOUT);
+        return;
+      }
+    }
+    if (P.stencil == kHeat) StageImpl<kHeat, DT, KH>::run_window(a, sm, w);
+    else StageImpl<kKS, DT, KK>::run_window(a, sm, w);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && (int64_t)idx != ba.drop_item) st_release(flags + w, s + 1);
+  }
+}
+
+template <class DT, int KH, int KK>
+cudaError_t launch_batch_t(const BatchArgs& ba, int grid, cudaStream_t s, bool query, int* capacity) {
+  constexpr int BMAX = 32 * (KH > KK ? KH : KK);
+  const size_t smem = stage_smem_bytes(BMAX);
+  cudaError_t e = cudaFuncSetAttribute(swept_batch_kernel<DT, KH, KK>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (query) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, swept_batch_kernel<DT, KH, KK>,
+                                                      kWarpsPerBlock * 32, smem);
+    *capacity = sms * (per_sm > 0 ? per_sm : 1);
+    return e;
+  }
+  swept_batch_kernel<DT, KH, KK><<<grid, kWarpsPerBlock * 32, smem, s>>>(ba);
+  return cudaGetLastError();
+}
+
+// Tile widths built for the batch: heat and KS each B in {256, 512}.
+template <class DT>
+cudaError_t launch_batch_dt(int KH, int KK, const BatchArgs& ba, int grid, cudaStream_t s, bool query,
+                            int* cap) {
+  if (KH == 8 && KK == 8) return launch_batch_t<DT, 8, 8>(ba, grid, s, query, cap);
+  if (KH == 8 && KK == 16) return launch_batch_t<DT, 8, 16>(ba, grid, s, query, cap);
+  if (KH == 16 && KK == 8) return launch_batch_t<DT, 16, 8>(ba, grid, s, query, cap);
+  if (KH == 16 && KK == 16) return launch_batch_t<DT, 16, 16>(ba, grid, s, query, cap);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch(int dtype, int KH, int KK, const BatchArgs& ba, int grid, cudaStream_t s,
+                         bool query, int* cap) {
+  return dtype == SWEPT_F64 ? launch_batch_dt<F64>(KH, KK, ba, grid, s, query, cap)
+                            : launch_batch_dt<F32C>(KH, KK, ba, grid, s, query, cap);
+}
+
+}  // namespace
+}  // namespace swept
+
+using swept::BatchArgs;
+using swept::BatchProblem;
+
+struct swept_batch_s {
+  int nprob, dtype, B_heat, B_ks, nstage_max, grid;
+  int64_t nitems, total_windows, pool_bytes;
+  unsigned char* edges;
+  int* flags;
+  BatchProblem* d_probs;
+  int64_t* d_cum;
+  int* d_nactive;
+  int64_t* d_stage_start;
+  unsigned long long* d_counter;
+  int* d_status;
+  double timeout_s;
+  int64_t drop_item;
+  // graph of one advance (memsets + the launch), rebuilt when the pool changes
+  cudaGraphExec_t exec;
+  void* graph_pool;
+  bool graph_valid;
+};
+
+namespace {
+
+int cuda_status_b(cudaError_t e) {
+  if (e == cudaSuccess) return SWEPT_OK;
+  if (e == cudaErrorMemoryAllocation) return SWEPT_ENOMEM;
+  return SWEPT_ECUDA;
+}
+
+int batch_consts(int stencil, const double* p, swept::Consts& c) {
+  std::memset(&c, 0, sizeof c);
+  if (stencil == SWEPT_HEAT) {
+    c.r = p[0];
+    c.r32 = (float)c.r;
+    return SWEPT_OK;
+  }
+  if (!(p[1] > 0.0)) return SWEPT_EINVAL;
+  const double dt = p[0], dx = p[1], dx2 = dx * dx;
+  c.a = -(dt / (4.0 * dx));
+  c.b = -(dt / dx2);
+  c.e = -(dt / (dx2 * dx2));
+  c.a32 = (float)c.a;
+  c.b32 = (float)c.b;
+  c.e32 = (float)c.e;
+  return SWEPT_OK;
+}
+
+void free_batch(swept_batch_s* b) {
+  if (!b) return;
+  if (b->graph_valid) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->edges);
+  cudaFree(b->flags);
+  cudaFree(b->d_probs);
+  cudaFree(b->d_cum);
+  cudaFree(b->d_nactive);
+  cudaFree(b->d_stage_start);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_status);
+  std::free(b);
+}
+
+BatchArgs make_args(const swept_batch_s* b, void* pool) {
+  BatchArgs a;
+  a.pool = static_cast<unsigned char*>(pool);
+  a.edges = b->edges;
+  a.flags = b->flags;
+  a.probs = b->d_probs;
+  a.cum = b->d_cum;
+  a.nactive = b->d_nactive;
+  a.stage_start = b->d_stage_start;
+  a.nstage_max = b->nstage_max;
+  a.nitems = b->nitems;
+  a.counter = b->d_counter;
+  a.status = b->d_status;
+  int dev = 0, khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (khz <= 0) khz = 2000000;
+  a.timeout_cycles = (long long)(b->timeout_s * (double)khz * 1000.0);
+  a.drop_item = b->drop_item;
+  return a;
+}
+
+cudaError_t enqueue(swept_batch_s* b, void* pool, cudaStream_t s) {
+  BatchArgs a = make_args(b, pool);
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->flags, 0, (size_t)b->total_windows * sizeof(int), s);
+  if (e == cudaSuccess && b->nitems > 0)
+    e = swept::launch_batch(b->dtype, b->B_heat / 32, b->B_ks / 32, a, b->grid, s, false, nullptr);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int swept_batch_plan(swept_batch_t* out, int nprob, const swept_problem_t* probs, int dtype, int B_heat,
+                     int B_ks) {
+  if (!out || nprob <= 0 || !probs) return SWEPT_EINVAL;
+  *out = nullptr;
+  if (dtype != SWEPT_F64 && dtype != SWEPT_F32C) return SWEPT_EINVAL;
+  if (B_heat == 0) B_heat = 512;
+  if (B_ks == 0) B_ks = 512;
+  if ((B_heat != 256 && B_heat != 512) || (B_ks != 256 && B_ks != 512)) return SWEPT_ENOTSUP;
+  std::vector<BatchProblem> h(nprob);
+  int64_t e_off = 0, f_off = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const swept_problem_t& p = probs[i];
+    if (p.stencil != SWEPT_HEAT && p.stencil != SWEPT_KS) return SWEPT_EINVAL;
+    const int B = p.stencil == SWEPT_HEAT ? B_heat : B_ks;
+    const int R = p.stencil == SWEPT_HEAT ? 1 : 2;
+    if (p.N <= 0 || p.N % B || p.nsteps < 0 || p.offset < 0 || (p.offset & 15)) return SWEPT_EINVAL;
+    if (p.N / B > (int64_t)0x7fffffff) return SWEPT_EINVAL;
+    BatchProblem& d = h[i];
+    std::memset(&d, 0, sizeof d);
+    if (batch_consts(p.stencil, p.params, d.c) != SWEPT_OK) return SWEPT_EINVAL;
+    d.u_off = p.offset;
+    d.N = p.N;
+    d.nwin = (int)(p.N / B);
+    d.B = B;
+    d.H = B / (2 * R);
+    d.stencil = p.stencil;
+    d.q = (int)(p.nsteps / d.H);
+    d.rem = (int)(p.nsteps % d.H);
+    d.nstages = p.nsteps == 0 ? 0 : (d.q == 0 ? 2 : (d.rem ? d.q + 2 : d.q + 1));
+    d.e_off = e_off;
+    d.f_off = f_off;
+    e_off += (int64_t)d.nwin * 2 * B * 8 * 2;
+    f_off += d.nwin;
+  }
+  std::stable_sort(h.begin(), h.end(),
+                   [](const BatchProblem& x, const BatchProblem& y) { return x.nstages > y.nstages; });
+  const int nstage_max = h[0].nstages;
+  std::vector<int64_t> cum(nprob + 1, 0);
+  for (int i = 0; i < nprob; ++i) cum[i + 1] = cum[i] + h[i].nwin;
+  std::vector<int> nactive(std::max(nstage_max, 1), 0);
+  std::vector<int64_t> stage_start(nstage_max + 1, 0);
+  for (int s = 0; s < nstage_max; ++s) {
+    int n = 0;
+    while (n < nprob && h[n].nstages > s) ++n;
+    nactive[s] = n;
+    stage_start[s + 1] = stage_start[s] + cum[n];
+  }
+  swept_batch_s* b = (swept_batch_s*)std::calloc(1, sizeof(swept_batch_s));
+  if (!b) return SWEPT_ENOMEM;
+  b->nprob = nprob;
+  b->dtype = dtype;
+  b->B_heat = B_heat;
+  b->B_ks = B_ks;
+  b->nstage_max = nstage_max;
+  b->nitems = stage_start[nstage_max];
+  b->total_windows = f_off;
+  b->timeout_s = 2.0;
+  b->drop_item = -1;
+  cudaError_t e = cudaMalloc((void**)&b->edges, (size_t)std::max<int64_t>(e_off, 16));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->flags, (size_t)std::max<int64_t>(f_off, 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_probs, sizeof(BatchProblem) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cum, sizeof(int64_t) * (nprob + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_nactive, sizeof(int) * nactive.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_stage_start, sizeof(int64_t) * (nstage_max + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_probs, h.data(), sizeof(BatchProblem) * nprob, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_cum, cum.data(), sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_nactive, nactive.data(), sizeof(int) * nactive.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_stage_start, stage_start.data(), sizeof(int64_t) * (nstage_max + 1),
+                   cudaMemcpyHostToDevice);
+  int cap = 0;
+  if (e == cudaSuccess) {
+    BatchArgs dummy = make_args(b, nullptr);
+    e = swept::launch_batch(dtype, B_heat / 32, B_ks / 32, dummy, 0, nullptr, true, &cap);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return cuda_status_b(e);
+  }
+  b->grid = cap > 0 ? cap : 1;
+  *out = b;
+  return SWEPT_OK;
+}
+
+int swept_batch_set(swept_batch_t b, int option, double value) {
+  if (!b) return SWEPT_EINVAL;
+  if (option == SWEPT_BOPT_TIMEOUT_S) {
+    if (!(value > 0.0) || value > 600.0) return SWEPT_EINVAL;
+    b->timeout_s = value;
+  } else if (option == SWEPT_BOPT_DROP_ITEM) {
+    b->drop_item = (int64_t)value;
+  } else if (option == SWEPT_BOPT_GRID) {
+    if (value < 1 || value > 1e6) return SWEPT_EINVAL;
+    b->grid = (int)value;
+  } else {
+    return SWEPT_EINVAL;
+  }
+  if (b->graph_valid) {            // the captured launch carries the old settings
+    cudaGraphExecDestroy(b->exec);
+    b->graph_valid = false;
+  }
+  return SWEPT_OK;
+}
+
+int swept_batch_info(swept_batch_t b, int64_t* info, int ninfo) {
+  if (!b || !info) return SWEPT_EINVAL;
+  const int64_t v[5] = {b->nitems, b->nstage_max, b->total_windows, b->grid, b->nprob};
+  for (int i = 0; i < ninfo && i < 5; ++i) info[i] = v[i];
+  return SWEPT_OK;
+}
+
+int swept_advance_batch(swept_batch_t b, void* pool, void* stream) {
+  if (!b || !pool || ((uintptr_t)pool & 15u)) return SWEPT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!b->graph_valid || b->graph_pool != pool) {
+    if (b->graph_valid) {
+      cudaGraphExecDestroy(b->exec);
+      b->graph_valid = false;
+    }
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status_b(e);
+    cudaGraph_t g;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue(b, pool, cs);
+      e = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+      }
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_status_b(e);
+    b->graph_valid = true;
+    b->graph_pool = pool;
+  }
+  return cuda_status_b(cudaGraphLaunch(b->exec, s));
+}
+
+int swept_batch_status(swept_batch_t b, void* stream) {
+  if (!b) return SWEPT_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return SWEPT_ECUDA;
+  int st = 0;
+  e = cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return SWEPT_ECUDA;
+  return st;
+}
+
+void swept_batch_destroy(swept_batch_t b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  free_batch(b);
+}
+
+}  // extern "C"

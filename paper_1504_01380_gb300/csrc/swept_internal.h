@@ -22,6 +22,13 @@ struct StageArgs {
   int hv;              // V-fill height (0 = load the flat state instead)
   int ht;              // trapezoid height (0 = none; h = full triangle)
   Consts c;
+  // Adjoint sweeps only: the forward trajectory of the segment, level n at
+  // tape + n*N (FP64), tape_len levels; the sweep's level tau uses the
+  // forward level tape_len - tau.  lev_fill / lev_trap: sweep level of the
+  // V-fill's base and of the trapezoid's flat base.
+  const double* tape;
+  int64_t tape_len;
+  int64_t lev_fill, lev_trap;
 };
 
 // Launchers, one per (stencil, dtype); K = B / 32.
@@ -29,6 +36,15 @@ cudaError_t launch_stage_heat_f64(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_heat_f32c(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_ks_f64(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_ks_f32c(int K, const StageArgs& a, cudaStream_t s);
+
+// Ring-pipelined full-diamond stage (hv = ht = h); nwarps <= 0 picks a size.
+cudaError_t launch_ring_heat_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+cudaError_t launch_ring_heat_f32c(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+cudaError_t launch_ring_ks_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+cudaError_t launch_ring_ks_f32c(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+
+// Adjoint (transposed KS, FP64) stage over a tape.
+cudaError_t launch_stage_ksadj_f64(int K, const StageArgs& a, cudaStream_t s);
 
 // Shared-memory bytes per block of the stage kernel for tile width B.
 inline size_t stage_smem_bytes(int B) { return (size_t)kWarpsPerBlock * 2 * B * 8; }

@@ -51,6 +51,22 @@ struct StageImpl {
   static constexpr int L = K / R;      // levels per phase
   static_assert(K % R == 0, "K must be a multiple of the stencil radius");
 
+  // Adjoint sweeps: the forward state at sweep level tau for this lane's K
+  // points (window start ws).  Unused (and compiled out) for forward stencils.
+  struct Coef {
+    double u[K];
+  };
+  static __device__ __forceinline__ void load_coef(Coef& cf, const StageArgs& a, int64_t ws, int lane,
+                                                   int64_t tau) {
+    if constexpr (ST == kKSAdj) {
+      int64_t g = ws + (int64_t)lane * K;
+      if (g >= a.N) g -= a.N;
+      ld_chunk<K>(a.tape + (a.tape_len - tau) * a.N + g, cf.u);
+    } else {
+      (void)cf; (void)a; (void)ws; (void)lane; (void)tau;
+    }
+  }
+
   // Placement for V-fill level mp = P*L + J: left arm at positions
   // 16K - R*mp - 2R + q, right arm at 16K + R*mp + q (level mp values).
   template <int J>
@@ -110,14 +126,17 @@ struct StageImpl {
 
   // Levels 1..hv of the V-fill; sL / sR hold the arms (level-major, 2r each).
   static __device__ __forceinline__ void vfill(Tile<DT, K>& t, const E* sL, const E* sR, int hv,
-                                               int lane, const Consts& c) {
+                                               int lane, const StageArgs& a, int64_t ws) {
+    const Consts& c = a.c;
     const int hmain = hv < H ? hv : H - 1;
+    Coef cf;
 #pragma unroll 1
     for (int mp = 0; mp < hmain; ++mp) {          // level mp values placed, mp+1 computed
       const int P = mp / L;
       const int j = mp - P * L;
+      load_coef(cf, a, ws, lane, a.lev_fill + mp + 1);
       select<0, L>(j, [&](auto J) { place<decltype(J)::value>(t, sL, sR, mp, P, lane); });
-      tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr);
+      tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr, cf.u);
     }
     if (hv == H) {
       // Last level: the arms reach r points beyond the window on each side.
@@ -134,7 +153,8 @@ struct StageImpl {
         if (lane == 31) t.put(K - R + q, vr);
         ovr[q] = Tile<DT, K>::hi_of(sR[mp * 2 * R + R + q]);
       }
-      tile_level<ST, DT, K, true>(t, c, lane, ovl, ovr);
+      load_coef(cf, a, ws, lane, a.lev_fill + H);
+      tile_level<ST, DT, K, true>(t, c, lane, ovl, ovr, cf.u);
     }
   }
 
@@ -142,10 +162,15 @@ struct StageImpl {
   // oL / oR.  On return the tile holds level ht-1 (the caller computes the
   // top level when ht < h).
   static __device__ __forceinline__ void trapezoid(Tile<DT, K>& t, E* oL, E* oR, int ht, int lane,
-                                                   const Consts& c) {
+                                                   const StageArgs& a, int64_t ws) {
+    const Consts& c = a.c;
+    Coef cf;
 #pragma unroll 1
     for (int m = 0; m < ht; ++m) {
-      if (m > 0) tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr);
+      if (m > 0) {
+        load_coef(cf, a, ws, lane, a.lev_trap + m);
+        tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr, cf.u);
+      }
       const int P = m / L;
       const int j = m - P * L;
       select<0, L>(j, [&](auto J) { capture<decltype(J)::value>(t, oL, oR, m, P, lane); });
@@ -161,9 +186,14 @@ struct StageImpl {
   }
 
   static __device__ void run(const StageArgs& a, E* sm) {
-    const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (w >= a.nwin) return;                     // warp-uniform
+    run_window(a, sm, w);
+  }
+
+  // The stage on window w (called by one whole warp).
+  static __device__ void run_window(const StageArgs& a, E* sm, int w) {
+    const int lane = threadIdx.x & 31;
     const int64_t N = a.N;
     const int64_t ws = (int64_t)w * B + a.offset;  // window start, < N
     E* sL = sm;
@@ -181,18 +211,20 @@ struct StageImpl {
       warp_copy(sL, ein + (int64_t)wl * (2 * B) + B, a.hv * 2 * R, lane);
       warp_copy(sR, ein + (int64_t)wr * (2 * B), a.hv * 2 * R, lane);
       __syncwarp();
-      vfill(t, sL, sR, a.hv, lane, a.c);
+      vfill(t, sL, sR, a.hv, lane, a, ws);
       __syncwarp();
     }
     if (a.ht > 0) {
-      trapezoid(t, sL, sR, a.ht, lane, a.c);
+      trapezoid(t, sL, sR, a.ht, lane, a, ws);
       __syncwarp();
       E* eout = static_cast<E*>(a.eout) + (int64_t)w * (2 * B);
       warp_copy(eout, sL, a.ht * 2 * R, lane);
       warp_copy(eout + B, sR, a.ht * 2 * R, lane);
       if (a.ht < H) {
         // top of the trapezoid: level ht on [r ht, B - r ht)
-        tile_level<ST, DT, K, false>(t, a.c, lane, nullptr, nullptr);
+        Coef cf;
+        load_coef(cf, a, ws, lane, a.lev_trap + a.ht);
+        tile_level<ST, DT, K, false>(t, a.c, lane, nullptr, nullptr, cf.u);
         const int lo = R * a.ht, hi = B - R * a.ht;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
