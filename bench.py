@@ -3,9 +3,10 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Workload: 1D heat, periodic, N = 2^24 points, r = 1/4, 20000 sub-timesteps
-per step, compensated FP32 state, tile B = 512; u0 = uniform[-1,1] noise
+per step, compensated FP32 state, tile B = 1024 (the fastest of the tile
+sweep B in {64, ..., 1024}, which is reported too); u0 = uniform[-1,1] noise
 plus 16 low modes.  One "step" is one swept_advance of the whole field
-through all 20000 sub-timesteps (q + 2 = 80 stage launches).
+through all 20000 sub-timesteps (q + 2 = 41 stage launches).
 
 Metric: cell-updates/s = N * nsteps / time.  Every step starts from the same
 device-resident input (restored outside the timed events); L2 is flushed
@@ -43,7 +44,7 @@ import workloads  # noqa: E402
 
 N_POINTS = 1 << 24
 NSTEPS = 20000
-TILE_B = 512
+TILE_B = 1024
 HEAT_R = 0.25
 METRIC = "cell-updates/s (N x steps / s), swept vs naive stepper, 1 GB300, at stated error"
 UNIT = "cell-updates/s"
@@ -52,7 +53,7 @@ OPS_PER_UPDATE_F64_HEAT = 3
 
 
 def workload_config(n_gpus: int):
-    return {"workload": "heat1d_periodic_N16777216_r0.25_20000steps_f32c_B512",
+    return {"workload": "heat1d_periodic_N16777216_r0.25_20000steps_f32c_B1024",
             "N": N_POINTS, "nsteps": NSTEPS, "B": TILE_B, "stencil": "heat 3-point forward Euler",
             "state": "f32 compensated (hi, lo)", "l2": "flushed between steps (256 MiB write)",
             "input": "device-resident, restored between steps", "parallelism": f"replicas x{n_gpus}"}
@@ -320,7 +321,7 @@ def run_gpu(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     # Dominant kernel: the ring-pipelined diamond kernel (heat, compensated
-    # FP32, K = 16), 77 of the 80 launches of a step.  achieved = useful FP32
+    # FP32, K = 32), 38 of the 41 launches of a step.  achieved = useful FP32
     # operations of the whole advance / its time; the three other launches
     # (first triangle, last fill, remainder) do less useful work per second,
     # so this is a lower bound on the ring kernel's own rate.
@@ -328,7 +329,7 @@ def run_gpu(args):
     avg_launch_s = (t_dev / args.steps) / launches_per_step
     peak_ops = 152 * 128 * sm_max * 1e6
     achieved = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * NSTEPS / (t_dev / args.steps)
-    roof = {"bound": "alu", "kernel": "swept_ring_kernel<heat,f32c,K=16>",
+    roof = {"bound": "alu", "kernel": "swept_ring_kernel<heat,f32c,K=32>",
             "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": achieved / peak_ops, "traffic": None,
             "per_launch_ops": per_launch_ops, "avg_launch_ms": avg_launch_s * 1e3,

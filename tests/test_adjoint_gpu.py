@@ -79,33 +79,56 @@ def test_autograd_function(cuda_lib):
     assert np.array_equal(g.cpu().numpy(), want)
 
 
-def test_ks_adjoint_full_size_vs_finite_differences(cuda_lib):
-    """N = 2^20, 20000 steps, checkpoints every 64 cycles: <grad J, v> vs central differences.
-
-    J = 1/2 sum u(T)^2; eps = 1e-6 per entry along seeded N(0,1) directions.  The
-    forward runs for the differences use the same swept advance (bit-exact with the
-    oracle's per-step stepping, checked elsewhere).
-    """
+def _J_factory(sw, plan, nsteps):
     import torch
-    sw = cuda_lib
-    n, nsteps = 1 << 20, 20000
-    u0 = workloads.ks_adjoint_state(n)
-    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, KS_PRM, sw.SWEPT_F64, 256)
-    red = []
 
     def J(u):
         t = dev(u)
         sw.swept_advance(plan, t, nsteps)
-        return 0.5 * float(torch.dot(t, t).item()), t
+        return sw.swept_reduce(plan, t, sw.SWEPT_HALF_SUMSQ).item(), t
+    return J
 
-    J0, uT = J(u0)
-    g = sw.swept_adjoint(plan, dev(u0), uT, nsteps, 64).cpu().numpy()
-    ndir = 8
-    for d in range(ndir):
+
+def test_ks_adjoint_full_size_short_horizon_fd(cuda_lib):
+    """N = 2^20, 2000 steps, 8 checkpoint segments: <grad J, v> within 1e-6 of central differences."""
+    sw = cuda_lib
+    n, nsteps = 1 << 20, 2000
+    u0 = workloads.ks_adjoint_state(n)
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, KS_PRM, sw.SWEPT_F64, 256)
+    J = _J_factory(sw, plan, nsteps)
+    _, uT = J(u0)
+    g = sw.swept_adjoint(plan, dev(u0), uT, nsteps, 2).cpu().numpy()
+    for d in range(8):
         v = workloads.fd_direction(n, d)
         eps = 1e-6
         fd = (J(u0 + eps * v)[0] - J(u0 - eps * v)[0]) / (2 * eps)
         ad = math.fsum(g * v)
-        red.append(abs(fd - ad) / abs(ad))
-    # chaos over 40 time units amplifies perturbations; record the agreement
-    assert max(red) <= 1e-4, red
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (d, fd, ad)
+
+
+def test_ks_adjoint_full_size_fd_converges(cuda_lib):
+    """N = 2^20, 20000 steps, checkpoints every 64 cycles (the adjoint workload).
+
+    Over 40 time units the chaotic dynamics amplify the O(eps^2) truncation of the
+    central difference, so agreement is checked by convergence: halving eps must
+    shrink |FD - AD| about fourfold (quadratic), i.e. FD tends to the adjoint.
+    """
+    sw = cuda_lib
+    n, nsteps = 1 << 20, 20000
+    u0 = workloads.ks_adjoint_state(n)
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, KS_PRM, sw.SWEPT_F64, 256)
+    J = _J_factory(sw, plan, nsteps)
+    _, uT = J(u0)
+    g = sw.swept_adjoint(plan, dev(u0), uT, nsteps, 64).cpu().numpy()
+    for d in range(4):
+        v = workloads.fd_direction(n, d)
+        ad = math.fsum(g * v)
+        errs = []
+        for eps in (1e-6, 5e-7, 2.5e-7):
+            fd = (J(u0 + eps * v)[0] - J(u0 - eps * v)[0]) / (2 * eps)
+            errs.append(abs(fd - ad) / abs(ad))
+        assert errs[0] <= 1e-2, (d, errs)
+        if errs[0] > 1e-4:           # truncation-dominated: must converge quadratically
+            assert errs[1] <= errs[0] / 2.5 and errs[2] <= errs[1] / 2.5, (d, errs)
+        else:                        # already at the rounding floor of J's differences
+            assert max(errs) <= 1e-3, (d, errs)
