@@ -356,15 +356,161 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------- other workloads (reports)
+def shard_problems(work, world: int):
+    """Split independent problems over ranks: greedy longest-first on N*steps.
+
+    Returns one index list per rank; every index appears exactly once.  The
+    batch needs no exchange between problems, so ranks share nothing but the
+    final max-time reduction.
+    """
+    loads = [0.0] * world
+    shards = [[] for _ in range(world)]
+    for i in sorted(range(len(work)), key=lambda j: -work[j]):
+        r = min(range(world), key=lambda k: (loads[k], k))
+        shards[r].append(i)
+        loads[r] += work[i]
+    return [sorted(x) for x in shards]
+
+
+def max_over_ranks(t: float, world: int, device=None) -> float:
+    """Max of a per-rank time over the process group (identity for one rank)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    x = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def run_batch_workload(args):
+    """4096 ragged problems (half heat, half KS), compensated FP32, one persistent launch."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    from paper_1504_01380_gb300 import tune
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    kinds, lengths, steps = workloads.batch_problems()
+    prm = {0: (HEAT_R, 0.0), 1: (workloads.KS_DT, workloads.KS_DX)}
+    allp = [(int(k), int(n), int(s), prm[int(k)]) for k, n, s in zip(kinds, lengths, steps)]
+    mine = shard_problems([n * s for _, n, s, _ in allp], world)[rank]
+    problems = [allp[i] for i in mine]
+    kinds, lengths, steps = kinds[mine], lengths[mine], steps[mine]
+    choice = tune.tune_batch(problems, sw.SWEPT_F32C)
+    batch = sw.swept_batch_plan(problems, sw.SWEPT_F32C, choice["B_heat"], choice["B_ks"])
+    states = workloads.batch_initial(kinds, lengths, seed_offsets=mine)
+    host = np.zeros(batch.pool_bytes, dtype=np.uint8)
+    pool = torch.tensor(host, device="cuda")
+    for off, u0 in zip(batch.offsets, states):
+        t = torch.tensor(u0, device="cuda")
+        seg = pool[off:off + 8 * len(u0)].view(torch.float32)
+        sw.swept_f32c_split(t, out=seg)
+    pristine = pool.clone()
+    total = float(np.sum(lengths.astype(np.float64) * steps))
+    for _ in range(args.warmup):
+        pool.copy_(pristine)
+        sw.swept_advance_batch(batch, pool)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        pool.copy_(pristine)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sw.swept_advance_batch(batch, pool)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    status = sw.swept_batch_status(batch)
+    t = max_over_ranks(sum(ms) / 1e3 / args.steps, world, torch.device("cuda", torch.cuda.current_device()))
+    if world > 1:
+        tot = torch.tensor([total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tot)
+        total = float(tot.item())
+    # baseline: one naive launch sequence per problem, on a seeded sample of 64 problems
+    rng = np.random.default_rng(1)
+    sample = rng.choice(len(problems), 64, replace=False)
+    naive_updates, naive_s = 0.0, 0.0
+    for i in sample:
+        st, n, ns, p = problems[i]
+        plan = sw.swept_plan(n, sw.RADIUS[st], st, p[: 1 if st == 0 else 2], sw.SWEPT_F32C, 0)
+        u = sw.swept_f32c_split(torch.tensor(states[i], device="cuda"))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sw.swept_naive_advance(plan, u, ns)
+        b.record()
+        torch.cuda.synchronize()
+        naive_s += a.elapsed_time(b) / 1e3
+        naive_updates += n * ns
+        plan.destroy()
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": total / t, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "dtype": "f32c", "data": "synthetic",
+            "config": {"workload": "batch_4096_ragged_heat_ks_f32c", "problems": len(problems),
+                       "sum_N_x_steps": total, "B_heat": choice["B_heat"], "B_ks": choice["B_ks"],
+                       "tuning": choice["rates"], **batch.info()},
+            "status": status,
+            "baseline_naive_per_problem": {"value": naive_updates / naive_s, "unit": UNIT,
+                                           "sample": "64 seeded problems, one launch per sub-timestep"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_adjoint_workload(args):
+    """Gradient of J = 1/2 sum u(T)^2 for KS N = 2^20, 20000 steps, FP64, checkpoints every 64 cycles."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    n, nsteps = 1 << 20, 20000
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, [workloads.KS_DT, workloads.KS_DX], sw.SWEPT_F64, 256)
+    u0 = torch.tensor(workloads.ks_adjoint_state(n), device="cuda")
+    uT = u0.clone()
+    sw.swept_advance(plan, uT, nsteps)
+    ms = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sw.swept_adjoint(plan, u0, uT, nsteps, 64)
+        b.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ms.append(a.elapsed_time(b))
+    t = sum(ms) / 1e3 / args.steps
+    f = u0.clone()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    sw.swept_advance(plan, f, nsteps)
+    b.record()
+    torch.cuda.synchronize()
+    fwd = a.elapsed_time(b) / 1e3
+    line = {"metric": METRIC, "value": n * nsteps / t, "unit": UNIT + " (forward-equivalent, gradient)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ks_adjoint_N1048576_20000steps_f64_B256_K64"},
+            "forward_only": {"value": n * nsteps / fwd, "unit": UNIT}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="heat", choices=["heat", "batch", "adjoint"],
+                    help="heat: the headline; batch / adjoint: report lines for those workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch_workload(args)
+    if args.workload == "adjoint":
+        return run_adjoint_workload(args)
     return run_gpu(args)
 
 

@@ -104,11 +104,17 @@ def batch_problems(count: int = 4096, nmin: int = 512, nmax: int = 262144,
     return kinds, lengths, steps
 
 
-def batch_initial(kinds: np.ndarray, lengths: np.ndarray, seed: int | None = None) -> list:
-    """One initial condition per batch problem (heat: noise + modes, KS: smoothed)."""
+def batch_initial(kinds: np.ndarray, lengths: np.ndarray, seed: int | None = None,
+                  seed_offsets=None) -> list:
+    """One initial condition per batch problem (heat: noise + modes, KS: smoothed).
+
+    Problem p of the full batch draws from seed base + 10000 + p; ``seed_offsets``
+    gives the full-batch index of each listed problem when a subset is passed.
+    """
     base = seed_for(3) if seed is None else seed
+    idx = list(range(len(kinds))) if seed_offsets is None else list(seed_offsets)
     out = []
-    for p, (kind, n) in enumerate(zip(kinds.tolist(), lengths.tolist())):
+    for p, kind, n in zip(idx, kinds.tolist(), lengths.tolist()):
         s = base + 10_000 + p
         out.append(heat_noise_modes(n, 16, s) if kind == 0 else ks_smoothed(n, s))
     return out
