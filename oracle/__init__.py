@@ -36,6 +36,8 @@ LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 
 HEAT = 0
 KS = 1
+HEAT_RK2 = 2
+KS_RK2 = 3
 
 _lock = threading.Lock()
 _lib = None
@@ -71,9 +73,12 @@ def lib():
             L.oracle_advance_f32c.argtypes = [i32, dp, fp, fp, i64, i64, i32]
             L.oracle_adjoint_f64.argtypes = [i32, dp, dp, dp, dp, i64, i64]
             L.oracle_adjoint_step_f64.argtypes = [i32, dp, dp, dp, dp, i64]
+            L.oracle_advance_rk2_f64.argtypes = [i32, dp, dp, i64, i64, i32]
+            L.oracle_rk2_substep_f64.argtypes = [i32, dp, i32, dp, dp, dp, i64]
             for f in ("oracle_step_f64", "oracle_advance_f64", "oracle_split_f32c",
                       "oracle_merge_f32c", "oracle_step_f32c", "oracle_advance_f32c",
-                      "oracle_adjoint_f64", "oracle_adjoint_step_f64", "oracle_max_threads"):
+                      "oracle_adjoint_f64", "oracle_adjoint_step_f64", "oracle_max_threads",
+                      "oracle_advance_rk2_f64", "oracle_rk2_substep_f64"):
                 getattr(L, f).restype = i32
             _lib = L
         return _lib
@@ -85,7 +90,7 @@ def _ptr(a: np.ndarray):
 
 def _params(stencil: int, params) -> np.ndarray:
     p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
-    need = 1 if stencil == HEAT else 2
+    need = 1 if stencil in (HEAT, HEAT_RK2) else 2
     if p.size != need:
         raise ValueError(f"stencil {stencil} takes {need} parameter(s), got {p.size}")
     return p
@@ -97,7 +102,7 @@ def _check(rc: int, what: str):
 
 
 def radius(stencil: int) -> int:
-    return 1 if stencil == HEAT else 2
+    return 1 if stencil in (HEAT, HEAT_RK2) else 2
 
 
 def step_f64(stencil: int, params, u: np.ndarray) -> np.ndarray:
@@ -176,6 +181,26 @@ def adjoint_step_f64(stencil: int, params, u: np.ndarray, lam: np.ndarray) -> np
     p = _params(stencil, params)
     _check(lib().oracle_adjoint_step_f64(stencil, _ptr(p), _ptr(u), _ptr(lam), _ptr(out), u.size),
            "adjoint_step_f64")
+    return out
+
+
+def advance_rk2_f64(stencil: int, params, u: np.ndarray, nsteps: int, threads: int = 0) -> np.ndarray:
+    """``nsteps`` two-stage Runge-Kutta (midpoint) time steps = 2*nsteps sub-timesteps."""
+    u = np.array(u, dtype=np.float64, copy=True, order="C")
+    p = _params(stencil, params)
+    _check(lib().oracle_advance_rk2_f64(stencil, _ptr(p), _ptr(u), u.size, int(nsteps), int(threads)),
+           "advance_rk2_f64")
+    return u
+
+
+def rk2_substep_f64(stencil: int, params, sub: int, u: np.ndarray, m: np.ndarray | None = None) -> np.ndarray:
+    """Sub-timestep A (sub=0: midpoint from u) or B (sub=1: next u from u and the midpoint m)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    m = u if m is None else np.ascontiguousarray(m, dtype=np.float64)
+    out = np.empty_like(u)
+    p = _params(stencil, params)
+    _check(lib().oracle_rk2_substep_f64(stencil, _ptr(p), int(sub), _ptr(u), _ptr(m), _ptr(out), u.size),
+           "rk2_substep_f64")
     return out
 
 

@@ -50,6 +50,19 @@
  *     Split: hi = (float)u, lo = (float)(u - (double)hi);
  *     merge: u = (double)hi + (double)lo.
  *
+ *   Two-stage Runge-Kutta (midpoint) as two sub-timesteps (Section 2: the
+ *   first sub-timestep forwards u and outputs the midpoint state, the second
+ *   outputs the next step from the forwarded u and the midpoint's
+ *   neighbours).  One time step = two sub-timesteps, each of radius r:
+ *       A: m = u + (dt/2) f(u)      B: u' = u + dt f(m)
+ *   with the FP64 increments written exactly as the forward-Euler ones
+ *   above, the constants halved for A (r/2; a/2, b/2, e/2, exact halvings):
+ *       heat A: w = (u[i-1] + u[i+1]) - 2u[i];  m = fma(r/2, w, u[i])
+ *       heat B: w = (m[i-1] + m[i+1]) - 2m[i];  u' = fma(r, w, u[i])
+ *       KS   A: m = fma(e/2, D(u), fma(b/2, W(u)[i], fma(a/2, t(u), u[i])))
+ *       KS   B: u' = fma(e, D(m), fma(b, W(m)[i], fma(a, t(m), u[i])))
+ *   with W, D, t the KS terms above evaluated on the argument.
+ *
  * Build: gcc -O2 -fopenmp -ffp-contract=off (no fast-math).  fma()/fmaf()
  * are the C library's correctly rounded fused multiply-adds.
  */
@@ -61,7 +74,7 @@
 #include <omp.h>
 #endif
 
-enum { OR_HEAT = 0, OR_KS = 1 };
+enum { OR_HEAT = 0, OR_KS = 1, OR_HEAT_RK2 = 2, OR_KS_RK2 = 3 };
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2 };
 
 typedef struct {
@@ -75,6 +88,12 @@ typedef struct {
 static int make_consts(int stencil, const double *prm, or_consts *c)
 {
     memset(c, 0, sizeof *c);
+    if (stencil == OR_HEAT_RK2 || stencil == OR_KS_RK2) {
+        /* same constants as the forward-Euler stencil; the RK2 drivers use them */
+        int rc = make_consts(stencil - 2, prm, c);
+        c->stencil = stencil;
+        return rc;
+    }
     c->stencil = stencil;
     if (stencil == OR_HEAT) {
         c->radius = 1;
@@ -249,6 +268,74 @@ int oracle_advance_f32c(int stencil, const double *prm, float *hi, float *lo, in
     }
     free(th);
     free(tl);
+    return OR_OK;
+}
+
+/* ----------------------------------------------------- RK2 (FP64) ----- */
+
+/* Increment of one Euler sub-timestep of size scale*dt applied to argument
+ * v at point i, added to base: the same expression as point_f64 with the
+ * constants multiplied by `scale` (1 or 1/2, exact) and the stencil read from
+ * v while the result is based on `base`. */
+static inline double rk2_sub(const or_consts *c, const double *v, double base, int64_t i, int64_t n,
+                             double scale)
+{
+    if (c->stencil == OR_HEAT_RK2) {
+        double s = v[wrap(i - 1, n)] + v[wrap(i + 1, n)];
+        double w = s - 2.0 * v[i];
+        return fma(scale * c->r, w, base);
+    } else {
+        double x[5];
+        for (int k = -2; k <= 2; ++k) x[k + 2] = v[wrap(i + k, n)];
+        double Gm = x[1] * x[1];
+        double Gp = x[3] * x[3];
+        double wm = (x[0] + x[2]) - 2.0 * x[1];
+        double w0 = (x[1] + x[3]) - 2.0 * x[2];
+        double wp = (x[2] + x[4]) - 2.0 * x[3];
+        double D = (wm + wp) - 2.0 * w0;
+        double t = Gp - Gm;
+        return fma(scale * c->e, D, fma(scale * c->b, w0, fma(scale * c->a, t, base)));
+    }
+}
+
+/* u <- u after nsteps RK2 time steps (2*nsteps sub-timesteps). */
+int oracle_advance_rk2_f64(int stencil, const double *prm, double *u, int64_t n, int64_t nsteps,
+                           int nthreads)
+{
+    or_consts c;
+    if (n <= 0 || nsteps < 0 || (stencil != OR_HEAT_RK2 && stencil != OR_KS_RK2) ||
+        make_consts(stencil, prm, &c) != OR_OK)
+        return OR_EINVAL;
+    if (nsteps == 0) return OR_OK;
+    double *m = (double *)malloc((size_t)n * sizeof(double));
+    double *tmp = (double *)malloc((size_t)n * sizeof(double));
+    if (!m || !tmp) { free(m); free(tmp); return OR_ENOMEM; }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) m[i] = rk2_sub(&c, u, u[i], i, n, 0.5);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) tmp[i] = rk2_sub(&c, m, u[i], i, n, 1.0);
+        memcpy(u, tmp, (size_t)n * sizeof(double));
+    }
+    free(m);
+    free(tmp);
+    return OR_OK;
+}
+
+/* One sub-timestep for tests: sub = 0 gives m from u; sub = 1 gives u' from (u, m). */
+int oracle_rk2_substep_f64(int stencil, const double *prm, int sub, const double *u, const double *m,
+                           double *out, int64_t n)
+{
+    or_consts c;
+    if (n <= 0 || (stencil != OR_HEAT_RK2 && stencil != OR_KS_RK2) || make_consts(stencil, prm, &c) != OR_OK)
+        return OR_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = sub == 0 ? rk2_sub(&c, u, u[i], i, n, 0.5) : rk2_sub(&c, m, u[i], i, n, 1.0);
     return OR_OK;
 }
 

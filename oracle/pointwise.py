@@ -44,11 +44,48 @@ def ks_point(v, a: float, b: float, e: float) -> float:
 
 
 def make_point_update(stencil: int, params):
-    """Return (radius, f) with f(values u[i-r..i+r]) -> u'[i]."""
+    """Return (radius, f) with f(values at i-r..i+r of level t, t) -> value at i of level t+1.
+
+    Forward Euler (stencils 0, 1): values are floats.  Two-stage Runge-Kutta
+    (stencils 2 heat, 3 KS; Section 2's two sub-timesteps with a forwarded
+    variable): values are pairs (u, m); even levels take sub-timestep A,
+    (u, m) -> (u, u + dt/2 f(u)), odd levels sub-timestep B,
+    (u, m) -> (u + dt f(m), m).  The second component after B is carried
+    along unchanged and never read.
+    """
     if stencil == 0:
         r = float(params[0])
-        return 1, (lambda v: heat_point(v[0], v[1], v[2], r))
+        return 1, (lambda v, t: heat_point(v[0], v[1], v[2], r))
     if stencil == 1:
         a, b, e = ks_constants(float(params[0]), float(params[1]))
-        return 2, (lambda v: ks_point(v, a, b, e))
+        return 2, (lambda v, t: ks_point(v, a, b, e))
+    if stencil == 2:
+        r = float(params[0])
+
+        def heat_rk2(v, t):
+            u0 = v[1][0]
+            if t % 2 == 0:
+                s = v[0][0] + v[2][0]
+                w = s - 2.0 * u0
+                return (u0, fma(0.5 * r, w, u0))
+            s = v[0][1] + v[2][1]
+            w = s - 2.0 * v[1][1]
+            return (fma(r, w, u0), v[1][1])
+        return 1, heat_rk2
+    if stencil == 3:
+        a, b, e = ks_constants(float(params[0]), float(params[1]))
+
+        def ks_rk2(v, t):
+            u0 = v[2][0]
+            if t % 2 == 0:
+                return (u0, ks_point([x[0] for x in v], 0.5 * a, 0.5 * b, 0.5 * e))
+            x = [y[1] for y in v]
+            Gm, Gp = x[1] * x[1], x[3] * x[3]
+            wm = (x[0] + x[2]) - 2.0 * x[1]
+            w0 = (x[1] + x[3]) - 2.0 * x[2]
+            wp = (x[2] + x[4]) - 2.0 * x[3]
+            D = (wm + wp) - 2.0 * w0
+            tt = Gp - Gm
+            return (fma(e, D, fma(b, w0, fma(a, tt, u0))), x[2])
+        return 2, ks_rk2
     raise ValueError(f"unknown stencil {stencil}")

@@ -49,7 +49,11 @@ class SweptTrace:
 
 
 def swept_simulate(stencil: int, params, u0, P: int, nsteps: int, max_stages: int = 100000):
-    """Run the swept stages on P nodes until level ``nsteps`` is known everywhere."""
+    """Run the swept stages on P nodes until level ``nsteps`` is known everywhere.
+
+    ``nsteps`` counts sub-timesteps (levels); a two-stage Runge-Kutta time step
+    is two of them.
+    """
     radius, f = make_point_update(stencil, params)
     N = len(u0)
     if P < 1 or N % P:
@@ -59,9 +63,11 @@ def swept_simulate(stencil: int, params, u0, P: int, nsteps: int, max_stages: in
         raise ValueError("points per node must be a multiple of 2r")
     # store[j]: (x, t) -> (value, origin); origin 'own' or ('recv', stage)
     store = [dict() for _ in range(P)]
+    pair = stencil in (2, 3)            # two-stage Runge-Kutta: (u, m) per point
     for j in range(P):
         for x in range(j * B, (j + 1) * B):
-            store[j][(x, 0)] = (float(u0[x]), "own")
+            v0 = float(u0[x])
+            store[j][(x, 0)] = ((v0, v0) if pair else v0, "own")
     count: dict = {}
     trace = SweptTrace(u_final=[], compute_count=count, stages=0)
 
@@ -103,7 +109,7 @@ def swept_simulate(stencil: int, params, u0, P: int, nsteps: int, max_stages: in
                         vals.append(v)
                         if origin != "own":
                             reads.setdefault(k[1], set()).add(k[0])
-                    S[(x, t + 1)] = (f(vals), "own")
+                    S[(x, t + 1)] = (f(vals, t), "own")
                     count[(x, t + 1)] = count.get((x, t + 1), 0) + 1
                     ncomp += 1
             stage_reads.append({lvl: sorted(xs) for lvl, xs in reads.items()})
@@ -135,6 +141,6 @@ def swept_simulate(stencil: int, params, u0, P: int, nsteps: int, max_stages: in
     for j in range(P):
         for (x, t), (v, _) in store[j].items():
             if t == nsteps and final[x] is None:
-                final[x] = v
+                final[x] = v[0] if pair else v
     trace.u_final = final
     return trace

@@ -490,3 +490,101 @@ def test_reductions_exact():
     assert R.total(u) == float(sum(Fraction(x) for x in u))
     assert R.dot(u, v) == float(sum(Fraction(x) * Fraction(y) for x, y in zip(u, v)))
     assert R.half_sumsq(u) == float(sum(Fraction(x) ** 2 for x in u) / 2)
+
+
+# --------------------------------------------------------------------------
+# Two-stage Runge-Kutta (midpoint) as two sub-timesteps (Section 2)
+# --------------------------------------------------------------------------
+
+HEAT_RK2, KS_RK2 = oracle.HEAT_RK2, oracle.KS_RK2
+
+
+@pytest.mark.parametrize("k", [1, 7, 64, 100])
+def test_heat_rk2_mode_gain(k):
+    """Mode k is scaled by 1 + z + z^2/2 per step, z = -4 r sin^2(pi k/N)."""
+    n, r, nsteps = 256, 0.25, 150
+    u0 = np.cos(2 * np.pi * k * np.arange(n) / n)
+    z = -4 * r * np.sin(np.pi * k / n) ** 2
+    got = oracle.advance_rk2_f64(HEAT_RK2, [r], u0, nsteps)
+    assert np.max(np.abs(got - (1 + z + z * z / 2) ** nsteps * u0)) <= 16 * nsteps * EPS
+
+
+@pytest.mark.parametrize("k", [1, 40, 128, 255])
+def test_ks_rk2_linear_mode_gain(k):
+    n = 512
+    dt, dx = KS_PRM
+    A = 1e-10
+    u0 = A * np.cos(2 * np.pi * k * np.arange(n) / n)
+    s = np.sin(np.pi * k / n) ** 2
+    z = dt * (4 * s / dx ** 2 - 16 * s ** 2 / dx ** 4)
+    u1 = oracle.advance_rk2_f64(KS_RK2, KS_PRM, u0, 1)
+    assert np.max(np.abs(u1 - (1 + z + z * z / 2) * u0)) <= 1e-9 * A
+
+
+def test_ks_rk2_second_order_in_time():
+    """Halving dt (twice the steps) moves the result by ~1/4 as much: the scheme is second order."""
+    n, dx = 256, 0.5
+    u0 = workloads.ks_smoothed(n, 3) * 10
+    T = 0.2
+    ref = oracle.advance_rk2_f64(KS_RK2, [T / 800, dx], u0, 800)
+    errs = [np.max(np.abs(oracle.advance_rk2_f64(KS_RK2, [T / m, dx], u0, m) - ref)) for m in (50, 100)]
+    assert 3.2 < errs[0] / errs[1] < 4.8
+
+
+@pytest.mark.parametrize("stencil,prm", [(HEAT_RK2, [0.25]), (KS_RK2, KS_PRM)])
+def test_rk2_conservation_and_symmetry(stencil, prm):
+    u0 = workloads.ks_smoothed(300, 8) * 10 if stencil == KS_RK2 else workloads.uniform(300, 8)
+    u = oracle.advance_rk2_f64(stencil, prm, u0, 200)
+    scale = math.fsum(np.abs(u0)) + math.fsum(np.abs(u))
+    assert abs(math.fsum(u) - math.fsum(u0)) <= 8 * 200 * EPS * scale
+    a = oracle.advance_rk2_f64(stencil, prm, np.roll(u0, 17), 50)
+    assert np.array_equal(a, np.roll(oracle.advance_rk2_f64(stencil, prm, u0, 50), 17))
+
+
+def exact_rk2_step(stencil, prm, u):
+    """One RK2 step with every operation's rounding emulated on rationals."""
+    n = len(u)
+    if stencil == HEAT_RK2:
+        r = prm[0]
+
+        def sub(v, base, scale):
+            return [X.fma64(X.mul64(scale, r), X.sub64(X.add64(v[i - 1], v[(i + 1) % n]), X.mul64(2.0, v[i])),
+                            base[i]) for i in range(n)]
+    else:
+        a, b, e = ks_consts64(*prm)
+
+        def sub(v, base, scale):
+            out = []
+            for i in range(n):
+                x = [v[(i + k) % n] for k in range(-2, 3)]
+                Gm, Gp = X.mul64(x[1], x[1]), X.mul64(x[3], x[3])
+                wm = X.sub64(X.add64(x[0], x[2]), X.mul64(2.0, x[1]))
+                w0 = X.sub64(X.add64(x[1], x[3]), X.mul64(2.0, x[2]))
+                wp = X.sub64(X.add64(x[2], x[4]), X.mul64(2.0, x[3]))
+                D = X.sub64(X.add64(wm, wp), X.mul64(2.0, w0))
+                t = X.sub64(Gp, Gm)
+                out.append(X.fma64(X.mul64(scale, e), D, X.fma64(X.mul64(scale, b), w0,
+                                                                  X.fma64(X.mul64(scale, a), t, base[i]))))
+            return out
+    m = sub(list(u), list(u), 0.5)
+    return np.array(sub(m, list(u), 1.0))
+
+
+@pytest.mark.parametrize("stencil,prm,scale", [(HEAT_RK2, [0.3], 1.0), (KS_RK2, KS_PRM, 5.0)])
+def test_rk2_step_ieee_exact(stencil, prm, scale):
+    u = workloads.uniform(16, 5) * scale
+    assert np.array_equal(oracle.advance_rk2_f64(stencil, prm, u, 1), exact_rk2_step(stencil, prm, u))
+
+
+@pytest.mark.parametrize("stencil,prm", [(HEAT_RK2, [0.25]), (KS_RK2, KS_PRM)])
+@pytest.mark.parametrize("B", [4, 8, 16])
+@pytest.mark.parametrize("nsteps", [1, 3, 4, 9, 20])
+def test_rk2_swept_bruteforce_matches_per_step(stencil, prm, B, nsteps):
+    """The swept stages with the forwarded pair (u, m) equal per-step RK2 (levels = 2 x steps)."""
+    n = 16
+    if B % (2 * oracle.radius(stencil)):
+        pytest.skip("B must be a multiple of 2r")
+    u0 = workloads.ks_smoothed(n, 91) * 10 if stencil == KS_RK2 else workloads.uniform(n, 91)
+    tr = swept_simulate(stencil, prm, u0, n // B, 2 * nsteps)
+    assert np.array_equal(np.array(tr.u_final), oracle.advance_rk2_f64(stencil, prm, u0, nsteps))
+    assert all(c == 1 for c in tr.compute_count.values())
