@@ -496,14 +496,55 @@ def run_adjoint_workload(args):
     return 0
 
 
+def run_ks_rk2_workload(args):
+    """KS by two-stage Runge-Kutta from u = 2cos(19x/128) (the paper's Section 6 scheme), FP64."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    n, nsteps = 1 << 22, 2500                      # 5000 sub-timesteps
+    prm = [workloads.KS_DT, workloads.KS_DX]
+    u0 = torch.tensor(workloads.ks_cosine(n), device="cuda")
+    res = {}
+    for B in (128, 256, 512):
+        plan = sw.swept_plan(n, 2, sw.SWEPT_KS_RK2, prm, sw.SWEPT_F64, B)
+        u = u0.clone()
+        sw.swept_advance(plan, u, nsteps)
+        ms = []
+        for _ in range(args.steps):
+            u.copy_(u0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            sw.swept_advance(plan, u, nsteps)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[str(B)] = n * nsteps / (sum(ms) / 1e3 / args.steps)
+        plan.destroy()
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS_RK2, prm, sw.SWEPT_F64, 256)
+    u = u0.clone()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    sw.swept_naive_advance(plan, u, nsteps)
+    b.record()
+    torch.cuda.synchronize()
+    naive = n * nsteps / (a.elapsed_time(b) / 1e3)
+    best = max(res, key=res.get)
+    line = {"metric": METRIC, "value": res[best], "unit": UNIT + " (time steps of 2 sub-timesteps)",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": n * nsteps / res[best] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ks_rk2_N4194304_2500steps_f64_cos19x128", "B": int(best)},
+            "tile_sweep": res, "naive": naive}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="heat", choices=["heat", "batch", "adjoint"],
-                    help="heat: the headline; batch / adjoint: report lines for those workloads")
+    ap.add_argument("--workload", default="heat", choices=["heat", "batch", "adjoint", "ks_rk2"],
+                    help="heat: the headline; batch / adjoint / ks_rk2: report lines for those workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -511,6 +552,8 @@ def main():
         return run_batch_workload(args)
     if args.workload == "adjoint":
         return run_adjoint_workload(args)
+    if args.workload == "ks_rk2":
+        return run_ks_rk2_workload(args)
     return run_gpu(args)
 
 

@@ -48,6 +48,13 @@ extern "C" {
  *               params[0] = dt, params[1] = dx.                            */
 #define SWEPT_HEAT  0
 #define SWEPT_KS    1
+/* Two-stage Runge-Kutta (midpoint) versions, FP64 only: one time step is two
+ * sub-timesteps (Section 2), A: m = u + dt/2 f(u) (u is forwarded) and
+ * B: u' = u + dt f(m), each of the stencil's radius; nsteps counts time
+ * steps.  The state in memory is u (double[N]); (u, m) pairs exist on chip
+ * and in the edge buffers.  Same parameters as the forward-Euler stencils. */
+#define SWEPT_HEAT_RK2  2
+#define SWEPT_KS_RK2    3
 
 /* Status codes. */
 #define SWEPT_OK         0
@@ -75,13 +82,14 @@ typedef struct swept_plan_s *swept_plan_t;
  * into N/B tiles of B points, each advanced by the stencil `stencil_id`
  * (radius `radius`, parameters `params[0..nparams)`) in arithmetic `dtype`.
  *   N       >= B, N % B == 0.
- *   radius  must equal the stencil's radius (1 heat, 2 KS).
+ *   radius  must equal the stencil's radius (1 heat, 2 KS, either time
+ *           integrator).
  *   B       tile width: 32*K points with K in {1,2,4,8,16,32}, K % radius
  *           == 0 (Section 3 asks for an even number of points per node; in
  *           general B % (2*radius) == 0).  B = 0 picks the tuned default.
  *   params  host pointer; copied.
- * Allocates the edge double-buffer (2 * 2N values, 32N bytes) on the
- * current device.  *out is set on success.
+ * Allocates the edge double-buffer (2 * 2N values, 32N bytes; 64N for the
+ * Runge-Kutta pairs) on the current device.  *out is set on success.
  * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP, SWEPT_ENOMEM, SWEPT_ECUDA.
  */
 int swept_plan(swept_plan_t *out, int64_t N, int radius, int stencil_id,
@@ -158,7 +166,8 @@ int swept_naive_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream
  *   u0, lambda_T, grad_u0  device double[N]; grad_u0 may not alias u0.
  * Scratch (plan-owned, grown on demand): (1 + segments + 2*K_cycles*h) * 8N
  * bytes for KS; none for heat.
- * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP (F32C plan), SWEPT_ENOMEM, SWEPT_ECUDA.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP (F32C or Runge-Kutta plan), SWEPT_ENOMEM,
+ * SWEPT_ECUDA.
  */
 int swept_adjoint(swept_plan_t plan, const void *u0, const void *lambda_T, void *grad_u0,
                   int64_t nsteps, int K_cycles, void *stream);
@@ -215,10 +224,11 @@ typedef struct swept_batch_s *swept_batch_t;
  *   dtype   SWEPT_F64 or SWEPT_F32C for the whole batch.
  *   B_heat, B_ks  tile widths for heat and KS problems, each 256 or 512
  *           (0 = 512); picked by the autotuner in the Python layer.
- * The work is one queue of (problem, window, stage) items in stage-major
- * order; a warp takes an item, waits (bounded) until the two windows of the
- * previous stage it reads from have published their edges, runs the stage
- * on its window and publishes.  Allocates per-problem edge buffers (32N
+ * The work is one queue of (problem, run of up to 8 windows, stage) items
+ * in stage-major order; a warp takes an item and, window by window, waits
+ * (bounded) until the two windows of the previous stage it reads from have
+ * published their edges, runs the stage and publishes.  Full diamond stages
+ * stream the run through the ring-pipelined kernel code.  Allocates per-problem edge buffers (32N
  * bytes each), per-window stage counters and the item tables.
  * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP, SWEPT_ENOMEM, SWEPT_ECUDA.
  */
@@ -231,8 +241,9 @@ int swept_batch_plan(swept_batch_t *out, int nprob, const swept_problem_t *probs
  *                         2): a wait that runs out records SWEPT_ETIMEOUT
  *                         and the launch winds down instead of hanging.
  *   SWEPT_BOPT_DROP_ITEM  test hook (a message lost on the host side): the
- *                         item with this queue index never publishes its
- *                         counter, so the items waiting on it time out.
+ *                         first window of the item with this queue index
+ *                         never publishes its counter, so the items waiting
+ *                         on it time out.
  *                         -1 = none (default).
  *   SWEPT_BOPT_GRID       number of thread blocks (default: all resident).
  */

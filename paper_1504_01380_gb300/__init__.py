@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
 
 SWEPT_F64, SWEPT_F32C = 0, 1
-SWEPT_HEAT, SWEPT_KS = 0, 1
+SWEPT_HEAT, SWEPT_KS, SWEPT_HEAT_RK2, SWEPT_KS_RK2 = 0, 1, 2, 3
 SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT = 0, 1, 2
 SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP = 0, -1, -2, -3, -4, -5
 SWEPT_ETOOBIG = -6
@@ -24,7 +24,7 @@ SWEPT_NOALLOC_MAX_N = 1 << 20
 SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS = 0, 1
 SWEPT_DIAMOND_AUTO, SWEPT_DIAMOND_WINDOW, SWEPT_DIAMOND_RING = 0, 1, 2
 
-RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2}
+RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2, SWEPT_HEAT_RK2: 1, SWEPT_KS_RK2: 2}
 
 # Every entry point declared in include/swept.h.
 EXPORTS = (

@@ -26,6 +26,7 @@ struct swept_plan_s {
   int ring_warps;         // 0 = automatic
   double* adj;            // adjoint scratch: work state, checkpoints, tape
   size_t adj_bytes;
+  int rk2;                // two-stage Runge-Kutta: 2 levels per step, pair edges
 };
 
 namespace {
@@ -41,6 +42,7 @@ int cuda_status(cudaError_t e) {
 // the FP64 values rounded to nearest.
 int make_consts(int stencil, const double* p, int np, Consts& c) {
   std::memset(&c, 0, sizeof c);
+  if (stencil == SWEPT_HEAT_RK2 || stencil == SWEPT_KS_RK2) stencil -= 2;   // same constants
   if (stencil == SWEPT_HEAT) {
     if (np < 1) return SWEPT_EINVAL;
     c.r = p[0];
@@ -65,6 +67,8 @@ int make_consts(int stencil, const double* p, int np, Consts& c) {
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
+  if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_stage_heatrk2_f64(p->K, a, s);
+  if (p->stencil == SWEPT_KS_RK2) return swept::launch_stage_ksrk2_f64(p->K, a, s);
   if (p->stencil == SWEPT_HEAT)
     return p->dtype == SWEPT_F64 ? swept::launch_stage_heat_f64(p->K, a, s)
                                  : swept::launch_stage_heat_f32c(p->K, a, s);
@@ -73,6 +77,8 @@ cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t
 }
 
 cudaError_t launch_ring(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
+  if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_ring_heatrk2_f64(p->K, a, p->ring_warps, s);
+  if (p->stencil == SWEPT_KS_RK2) return swept::launch_ring_ksrk2_f64(p->K, a, p->ring_warps, s);
   if (p->stencil == SWEPT_HEAT)
     return p->dtype == SWEPT_F64 ? swept::launch_ring_heat_f64(p->K, a, p->ring_warps, s)
                                  : swept::launch_ring_heat_f32c(p->K, a, p->ring_warps, s);
@@ -121,10 +127,12 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
                int nparams, int dtype, int B) {
   if (!out || !params) return SWEPT_EINVAL;
   *out = nullptr;
-  if (stencil_id != SWEPT_HEAT && stencil_id != SWEPT_KS) return SWEPT_EINVAL;
-  const int rad = stencil_id == SWEPT_HEAT ? 1 : 2;
+  if (stencil_id < SWEPT_HEAT || stencil_id > SWEPT_KS_RK2) return SWEPT_EINVAL;
+  const int rad = (stencil_id == SWEPT_HEAT || stencil_id == SWEPT_HEAT_RK2) ? 1 : 2;
   if (radius != rad) return SWEPT_EINVAL;
   if (dtype != SWEPT_F64 && dtype != SWEPT_F32C) return SWEPT_EINVAL;
+  const bool rk2 = stencil_id >= SWEPT_HEAT_RK2;
+  if (rk2 && dtype != SWEPT_F64) return SWEPT_ENOTSUP;
   if (N <= 0) return SWEPT_EINVAL;
   if (B == 0) B = default_B(N, rad);
   if (B <= 0 || B % 32) return SWEPT_EINVAL;
@@ -150,8 +158,9 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->prm[0] = params[0];
   p->prm[1] = nparams > 1 ? params[1] : 0.0;
   p->c = c;
+  p->rk2 = rk2 ? 1 : 0;
   cudaGetDevice(&p->device);
-  p->edge_half = (size_t)p->nwin * 2 * B * 8;
+  p->edge_half = (size_t)p->nwin * 2 * B * (rk2 ? 16 : 8);
   cudaError_t e = cudaMalloc((void**)&p->edges, 2 * p->edge_half);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->red, 2 * swept::kReduceBlocks * sizeof(double));
   if (e != cudaSuccess) {
@@ -199,9 +208,10 @@ int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
   if (nsteps == 0) return SWEPT_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  const int64_t levels = p->rk2 ? 2 * nsteps : nsteps;    // sub-timesteps
   const int64_t H = p->H;
-  const int64_t q = nsteps / H;
-  const int rem = (int)(nsteps % H);
+  const int64_t q = levels / H;
+  const int rem = (int)(levels % H);
   unsigned char* buf[2] = {p->edges, p->edges + p->edge_half};
   StageArgs a{};
   a.u = u;
@@ -217,6 +227,8 @@ int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     a.ht = ht;
     a.ein = buf[(k + 1) & 1];
     a.eout = buf[k & 1];
+    a.lev_fill = k >= 1 ? (k - 1) * H : 0;      // absolute levels (Runge-Kutta parity)
+    a.lev_trap = k * H;
     if (ring && hv == p->H && ht == p->H) return launch_ring(p, a, s);
     return launch_stage(p, a, s);
   };
@@ -283,7 +295,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
                   int K_cycles, void* stream) {
   if (!p || !u0 || !lam_T || !grad || nsteps < 0) return SWEPT_EINVAL;
   if (!aligned16(u0) || !aligned16(lam_T) || !aligned16(grad)) return SWEPT_EINVAL;
-  if (p->dtype != SWEPT_F64) return SWEPT_ENOTSUP;
+  if (p->dtype != SWEPT_F64 || p->rk2) return SWEPT_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)p->N * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(grad, lam_T, bytes, cudaMemcpyDeviceToDevice, s);
@@ -340,6 +352,21 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
 int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->rk2) {
+    // per time step: m = A(u) into scratch, then u' = B(u, m) into scratch, swap
+    double* m = reinterpret_cast<double*>(p->edges);
+    double* bufs[2] = {static_cast<double*>(u), m + p->N};
+    cudaError_t e = cudaSuccess;
+    int cur = 0;
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+      e = swept::launch_naive_rk2(p->stencil, 0, bufs[cur], nullptr, m, p->N, p->c, s);
+      if (e == cudaSuccess) e = swept::launch_naive_rk2(p->stencil, 1, bufs[cur], m, bufs[cur ^ 1], p->N, p->c, s);
+      cur ^= 1;
+    }
+    if (e == cudaSuccess && cur == 1)
+      e = cudaMemcpyAsync(u, bufs[1], (size_t)p->N * 8, cudaMemcpyDeviceToDevice, s);
+    return cuda_status(e);
+  }
   void* bufs[2] = {u, p->edges};
   cudaError_t e = cudaSuccess;
   int cur = 0;

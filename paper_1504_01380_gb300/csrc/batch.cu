@@ -1,9 +1,12 @@
 // Batched persistent swept launch: many independent periodic problems of
 // uneven length and step count advanced by one kernel launch.
 //
-// Work items are (problem, window, stage) triples, one swept stage of one
-// window (Section 3's per-node stage), processed by one warp with the same
-// code as the per-window stage kernel.  Items are handed out by one atomic
+// Work items are (problem, run of up to RL consecutive windows, stage), one
+// swept stage of those windows (Section 3's per-node stage), processed by one
+// warp: full diamond stages stream the run through the ring-pipelined kernel
+// code (fill of one window overlapped with the triangle of the previous);
+// other stages (first triangle, last fill, remainder) go window by window with
+// the per-window stage code.  Items are handed out by one atomic
 // counter in stage-major order over the whole batch: every stage-s item of
 // every problem precedes every stage-(s+1) item.  A stage-s item (s >= 1)
 // reads the leading edges of the two stage-(s-1) windows it straddles, so it
@@ -32,6 +35,7 @@
 
 #include "swept.h"
 #include "swept_internal.h"
+#include "swept_ring.cuh"
 #include "swept_stage.cuh"
 
 namespace swept {
@@ -41,7 +45,7 @@ struct BatchProblem {
   int64_t e_off;          // byte offset of the edge double buffer in the plan's edge pool
   int64_t f_off;          // index of the first window counter
   int64_t N;
-  int nwin, B, H, stencil, q, rem, nstages, pad;
+  int nwin, B, H, stencil, q, rem, nstages, nruns;
   Consts c;
 };
 
@@ -50,7 +54,7 @@ struct BatchArgs {
   unsigned char* edges;
   int* flags;
   const BatchProblem* probs;    // sorted by nstages, descending
-  const int64_t* cum;           // nprob + 1: windows before problem i (sorted order)
+  const int64_t* cum;           // nprob + 1: runs before problem i (sorted order)
   const int* nactive;           // per stage: problems still active (a prefix)
   const int64_t* stage_start;   // nstage_max + 1: first item of each stage
   int nstage_max;
@@ -58,7 +62,8 @@ struct BatchArgs {
   unsigned long long* counter;
   int* status;
   long long timeout_cycles;
-  int64_t drop_item;            // item whose counter is never published (-1: none)
+  int64_t drop_item;            // item whose first window never publishes (-1: none)
+  int run_len;                  // windows per item
 };
 
 namespace {
@@ -107,6 +112,44 @@ __host__ __device__ __forceinline__ void stage_shape(int s, int q, int rem, int 
   }
 }
 
+// Dependence hooks of one item: wait (bounded) for the two windows of the
+// previous stage a window reads from; publish a window after its edges.
+struct BatchHooks {
+  int* flags;
+  int* status;
+  long long budget;
+  int s, nwin, offset, lane;
+  int drop_w;                   // window that must not publish (-1: none)
+  __device__ __forceinline__ bool ready(int w) const {
+    if (s == 0) return true;
+    const int wl = offset ? w : (w == 0 ? nwin - 1 : w - 1);
+    const int wr = offset ? (w + 1 == nwin ? 0 : w + 1) : w;
+    const long long t0 = clock64();
+    bool ok = wait_ge(flags + wl, s, t0, budget);
+    if (ok) ok = wait_ge(flags + wr, s, t0, budget);
+    ok = __all_sync(kFull, ok);
+    if (!ok && lane == 0) atomicCAS(status, 0, SWEPT_ETIMEOUT);
+    return ok;
+  }
+  __device__ __forceinline__ void done(int w) const {
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && w != drop_w) st_release(flags + w, s + 1);
+  }
+};
+
+template <int ST, class DT, int K>
+__device__ __forceinline__ bool batch_item(const StageArgs& a, typename DT::E* sm, int w0, int w1,
+                                           const BatchHooks& hk, int H) {
+  if (a.hv == H && a.ht == H) return RingImpl<ST, DT, K>::run_hooked(a, sm, w0, w1, hk);
+  for (int w = w0; w < w1; ++w) {
+    if (!hk.ready(w)) return false;
+    StageImpl<ST, DT, K>::run_window(a, sm, w);
+    hk.done(w);
+  }
+  return true;
+}
+
 template <class DT, int KH, int KK>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 swept_batch_kernel(const BatchArgs ba) {
@@ -124,9 +167,11 @@ swept_batch_kernel(const BatchArgs ba) {
     const int s = upper_index<int64_t>(ba.stage_start, ba.nstage_max, (int64_t)idx);
     const int64_t k = (int64_t)idx - ba.stage_start[s];
     const int i = upper_index<int64_t>(ba.cum, ba.nactive[s], k);
-    const int w = (int)(k - ba.cum[i]);
+    const int run = (int)(k - ba.cum[i]);
     const BatchProblem P = ba.probs[i];
-    StageArgs a;
+    const int w0 = run * ba.run_len;
+    const int w1 = min(w0 + ba.run_len, P.nwin);
+    StageArgs a{};
     a.u = ba.pool + P.u_off;
     a.N = P.N;
     a.nwin = P.nwin;
@@ -137,23 +182,18 @@ swept_batch_kernel(const BatchArgs ba) {
     a.ein = eb + ((s + 1) & 1) * half;
     a.eout = eb + (s & 1) * half;
     a.c = P.c;
-    int* flags = ba.flags + P.f_off;
-    if (s > 0) {
-      const int wl = a.offset ? w : (w == 0 ? P.nwin - 1 : w - 1);
-      const int wr = a.offset ? (w + 1 == P.nwin ? 0 : w + 1) : w;
-      const long long t0 = clock64();
-      bool ok = wait_ge(flags + wl, s, t0, ba.timeout_cycles);
-      if (ok) ok = wait_ge(flags + wr, s, t0, ba.timeout_cycles);
-      if (!__all_sync(kFull, ok)) {
-        if (lane == 0) atomicCAS(ba.status, 0, SWEPT_ETIMEOUT);
-        return;
-      }
-    }
-    if (P.stencil == kHeat) StageImpl<kHeat, DT, KH>::run_window(a, sm, w);
-    else StageImpl<kKS, DT, KK>::run_window(a, sm, w);
-    __threadfence();
-    __syncwarp();
-    if (lane == 0 && (int64_t)idx != ba.drop_item) st_release(flags + w, s + 1);
+    BatchHooks hk;
+    hk.flags = ba.flags + P.f_off;
+    hk.status = ba.status;
+    hk.budget = ba.timeout_cycles;
+    hk.s = s;
+    hk.nwin = P.nwin;
+    hk.offset = a.offset;
+    hk.lane = lane;
+    hk.drop_w = (int64_t)idx == ba.drop_item ? w0 : -1;
+    const bool ok = P.stencil == kHeat ? batch_item<kHeat, DT, KH>(a, sm, w0, w1, hk, P.H)
+                                       : batch_item<kKS, DT, KK>(a, sm, w0, w1, hk, P.H);
+    if (!ok) return;
   }
 }
 
@@ -221,6 +261,10 @@ struct swept_batch_s {
 
 namespace {
 
+// Windows per work item: the ring pays one extra half-slot per item, so the
+// item keeps 1/(kRunLen + 1) of its slots partly idle.
+constexpr int kRunLen = 8;
+
 int cuda_status_b(cudaError_t e) {
   if (e == cudaSuccess) return SWEPT_OK;
   if (e == cudaErrorMemoryAllocation) return SWEPT_ENOMEM;
@@ -278,6 +322,7 @@ BatchArgs make_args(const swept_batch_s* b, void* pool) {
   if (khz <= 0) khz = 2000000;
   a.timeout_cycles = (long long)(b->timeout_s * (double)khz * 1000.0);
   a.drop_item = b->drop_item;
+  a.run_len = kRunLen;
   return a;
 }
 
@@ -324,6 +369,7 @@ int swept_batch_plan(swept_batch_t* out, int nprob, const swept_problem_t* probs
     d.q = (int)(p.nsteps / d.H);
     d.rem = (int)(p.nsteps % d.H);
     d.nstages = p.nsteps == 0 ? 0 : (d.q == 0 ? 2 : (d.rem ? d.q + 2 : d.q + 1));
+    d.nruns = (d.nwin + kRunLen - 1) / kRunLen;
     d.e_off = e_off;
     d.f_off = f_off;
     e_off += (int64_t)d.nwin * 2 * B * 8 * 2;
@@ -333,7 +379,7 @@ int swept_batch_plan(swept_batch_t* out, int nprob, const swept_problem_t* probs
                    [](const BatchProblem& x, const BatchProblem& y) { return x.nstages > y.nstages; });
   const int nstage_max = h[0].nstages;
   std::vector<int64_t> cum(nprob + 1, 0);
-  for (int i = 0; i < nprob; ++i) cum[i + 1] = cum[i] + h[i].nwin;
+  for (int i = 0; i < nprob; ++i) cum[i + 1] = cum[i] + h[i].nruns;
   std::vector<int> nactive(std::max(nstage_max, 1), 0);
   std::vector<int64_t> stage_start(nstage_max + 1, 0);
   for (int s = 0; s < nstage_max; ++s) {

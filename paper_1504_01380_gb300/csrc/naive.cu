@@ -73,7 +73,64 @@ cudaError_t launch(const void* in, void* out, int64_t N, const Consts& c, cudaSt
   return cudaGetLastError();
 }
 
+// Runge-Kutta sub-timestep on the whole field: sub 0 writes m = A(u) to out,
+// sub 1 writes u' = B(u, m) to out.
+template <int ST>
+__global__ void __launch_bounds__(kNaiveThreads)
+naive_rk2_kernel(int sub, const double* __restrict__ u, const double* __restrict__ m,
+                 double* __restrict__ out, int64_t N, const Consts c) {
+  constexpr int R = Radius<ST>::value;
+  const int lane = threadIdx.x & 31;
+  const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
+  const bool valid = i0 < N;
+  const double* arg = sub == 0 ? u : m;
+  Tile<F64P, kV> t;
+  t.zero();
+  if (valid) {
+    ld_chunk<kV>(u + i0, t.u);
+    ld_chunk<kV>(arg + i0, t.m);
+  }
+  double x[kV + 2 * R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    x[i] = __shfl_sync(kFull, t.m[kV - R + i], (lane + 31) & 31);
+    x[R + kV + i] = __shfl_sync(kFull, t.m[i], (lane + 1) & 31);
+  }
+#pragma unroll
+  for (int k = 0; k < kV; ++k) x[R + k] = t.m[k];
+  if (!valid) return;
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      int64_t g = i0 - R + i;
+      if (g < 0) g += N;
+      x[i] = arg[g];
+    }
+  }
+  if (lane == 31 || i0 + kV >= N) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      int64_t g = i0 + kV + i;
+      if (g >= N) g -= N;
+      x[R + kV + i] = arg[g];
+    }
+  }
+  RK2Core<ST, kV>::apply(t, x, c, sub);
+  st_chunk<kV>(out + i0, sub == 0 ? t.m : t.u);
+}
+
 }  // namespace
+
+cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
+                             const Consts& c, cudaStream_t s) {
+  if (N % kV) return cudaErrorInvalidValue;
+  const int64_t grid = (N / kV + kNaiveThreads - 1) / kNaiveThreads;
+  if (stencil == 2)
+    naive_rk2_kernel<kHeatRK2><<<(unsigned)grid, kNaiveThreads, 0, s>>>(sub, u, m, out, N, c);
+  else
+    naive_rk2_kernel<kKSRK2><<<(unsigned)grid, kNaiveThreads, 0, s>>>(sub, u, m, out, N, c);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_naive_step(int stencil, int dtype, const void* in, void* out, int64_t N,
                               const Consts& c, cudaStream_t s) {

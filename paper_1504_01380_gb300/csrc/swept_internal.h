@@ -46,8 +46,18 @@ cudaError_t launch_ring_ks_f32c(int K, const StageArgs& a, int nwarps, cudaStrea
 // Adjoint (transposed KS, FP64) stage over a tape.
 cudaError_t launch_stage_ksadj_f64(int K, const StageArgs& a, cudaStream_t s);
 
-// Shared-memory bytes per block of the stage kernel for tile width B.
-inline size_t stage_smem_bytes(int B) { return (size_t)kWarpsPerBlock * 2 * B * 8; }
+// Two-stage Runge-Kutta stencils (FP64, state pairs (u, m) on chip).
+cudaError_t launch_stage_heatrk2_f64(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ksrk2_f64(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_ring_heatrk2_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+cudaError_t launch_ring_ksrk2_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+// Naive Runge-Kutta sub-timestep: sub 0: m = A(u); sub 1: out = B(u, m).
+cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
+                             const Consts& c, cudaStream_t s);
+
+// Shared-memory bytes per block of the stage kernel for tile width B and
+// edge elements of esize bytes (8; 16 for the Runge-Kutta pair).
+inline size_t stage_smem_bytes(int B, int esize = 8) { return (size_t)kWarpsPerBlock * 2 * B * esize; }
 
 // Naive per-step stepper: out = S(in).
 cudaError_t launch_naive_step(int stencil, int dtype, const void* in, void* out, int64_t N,

@@ -12,12 +12,18 @@
 // ring (lane 31's right neighbour is lane 0).  The window being filled sits
 // at ring offset c (0 or M/2), the window being emptied at c + M/2; the two
 // regions are separated by two gaps of 16r slots.  Each level:
-//   1. the triangle's leading edges of the previous level (2r values on each
-//      side, adjacent to the gaps) are captured to shared memory;
-//   2. the V's arm values of the previous level (2r per side, read from the
-//      previous stage's edges) are placed into the gaps, where the fill's
-//      boundary points read them;
+//   1. the V's arm values of the previous level (2r per side, from the
+//      previous stage's edges, staged in shared memory at the slot's start)
+//      are read, and the triangle's leading edges of the previous level (2r
+//      values on each side, adjacent to the gaps) are captured into the same
+//      shared-memory slots, which are free once read;
+//   2. the arm values are placed into the gaps, where the fill's boundary
+//      points read them;
 //   3. all M slots are advanced one level.
+// At the end of the slot the captured edges go to global memory in one
+// coalesced copy.  (Streaming the arms in small cp.async chunks and storing
+// captures straight to global memory cuts shared memory to 2 KB per warp, but
+// measured 6% slower at K = 32, where registers bind the occupancy anyway.)
 // After h levels the filled window is flat and becomes the window being
 // emptied in the next slot (same offset), and the next window is filled at
 // the other offset.  A run of n windows takes n + 1 slots; the first slot
@@ -101,11 +107,28 @@ struct RingImpl {
                                                    int lane) {
     const uint4* s4 = reinterpret_cast<const uint4*>(src);
     uint4* d4 = reinterpret_cast<uint4*>(dst);
-    for (int i = lane; i < n / 2; i += 32) d4[i] = s4[i];
+    const int n16 = n * (int)sizeof(E) / 16;
+    for (int i = lane; i < n16; i += 32) d4[i] = s4[i];
   }
 
+  // Hooks of a run without dependences (one launch per stage).
+  struct NoHooks {
+    __device__ __forceinline__ bool ready(int) const { return true; }
+    __device__ __forceinline__ void done(int) const {}
+  };
+
   // One warp: windows [w0, w1) of a full diamond stage (hv = ht = h).
+  // sm: 2B elements of shared memory.
   static __device__ void run(const StageArgs& a, E* sm, int w0, int w1) {
+    run_hooked(a, sm, w0, w1, NoHooks{});
+  }
+
+  // As run(), with hooks for runs whose inputs are produced concurrently:
+  // hk.ready(w) is called (by the whole warp) before any arm value of window
+  // w is read and returns false when the wait for it gave up; hk.done(w) is
+  // called after window w's edges are stored.  Returns false if a wait gave up.
+  template <class Hooks>
+  static __device__ bool run_hooked(const StageArgs& a, E* sm, int w0, int w1, const Hooks& hk) {
     const int lane = threadIdx.x & 31;
     const E* ein = static_cast<const E*>(a.ein);
     E* eout = static_cast<E*>(a.eout);
@@ -122,6 +145,7 @@ struct RingImpl {
       const int cl = (slot & 1) ? 16 : 0;          // ring offset of the filled window, in lanes
       if (fill) {
         const int w = w0 + slot;
+        if (!hk.ready(w)) return false;
         const int wl = a.offset ? w : (w == 0 ? a.nwin - 1 : w - 1);
         const int wr = a.offset ? (w + 1 == a.nwin ? 0 : w + 1) : w;
         warp_copy(s0, ein + (int64_t)wl * (2 * B) + B, B, lane);
@@ -144,7 +168,10 @@ struct RingImpl {
           if (empty) capture_all<J>(t, s0, s1, mp, P, cl, lane, std::make_integer_sequence<int, 2 * R>{});
           if (fill) place_all<J>(t, al, ar, P, cl, lane, std::make_integer_sequence<int, 2 * R>{});
         });
-        tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr);
+        // Runge-Kutta: both windows are at levels of the same parity (h is
+        // even), so one sub-timestep serves the whole ring
+        tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, nullptr,
+                                     IsRK2<ST>::value ? (int)((a.lev_fill + mp) & 1) : 0);
         if (++j == L) { j = 0; ++P; }
       }
       __syncwarp();
@@ -152,19 +179,26 @@ struct RingImpl {
         const int ws = w0 + slot - 1;
         warp_copy(eout + (int64_t)ws * (2 * B), s0, B, lane);
         warp_copy(eout + (int64_t)ws * (2 * B) + B, s1, B, lane);
+        hk.done(ws);
       }
       __syncwarp();
     }
+    return true;
   }
 };
+
+// Shared memory of the ring kernel per block: 2B elements per warp.
+template <int ST, class DT, int K>
+size_t ring_smem_bytes() {
+  return stage_smem_bytes(32 * K, (int)sizeof(typename DT::E));
+}
 
 template <int ST, class DT, int K>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 swept_ring_kernel(const StageArgs a, int nwarps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
-  constexpr int B = 32 * K;
-  E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * B);
+  E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * 32 * K);
   const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (gw >= nwarps) return;
   // balanced contiguous runs: warp gw takes [gw*n/W, (gw+1)*n/W)
@@ -177,8 +211,7 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
 // nwin / 2), so that every warp streams at least two windows when it can.
 template <int ST, class DT, int K>
 cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
-  constexpr int B = 32 * K;
-  const size_t smem = stage_smem_bytes(B);
+  const size_t smem = ring_smem_bytes<ST, DT, K>();
   cudaError_t e = cudaFuncSetAttribute(swept_ring_kernel<ST, DT, K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

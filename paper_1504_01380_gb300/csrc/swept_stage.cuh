@@ -53,8 +53,11 @@ struct StageImpl {
 
   // Adjoint sweeps: the forward state at sweep level tau for this lane's K
   // points (window start ws).  Unused (and compiled out) for forward stencils.
+  // Runge-Kutta stencils: the sub-timestep of sweep level tau is A when the
+  // input level tau - 1 is even, B when it is odd.
   struct Coef {
     double u[K];
+    int sub = 0;
   };
   static __device__ __forceinline__ void load_coef(Coef& cf, const StageArgs& a, int64_t ws, int lane,
                                                    int64_t tau) {
@@ -62,9 +65,18 @@ struct StageImpl {
       int64_t g = ws + (int64_t)lane * K;
       if (g >= a.N) g -= a.N;
       ld_chunk<K>(a.tape + (a.tape_len - tau) * a.N + g, cf.u);
+    } else if constexpr (IsRK2<ST>::value) {
+      cf.sub = (int)((tau - 1) & 1);
+      (void)a; (void)ws; (void)lane;
     } else {
       (void)cf; (void)a; (void)ws; (void)lane; (void)tau;
     }
+  }
+  // The value a neighbour contributes to the stencil: u (or hi); for the
+  // Runge-Kutta pair, u in sub-timestep A and m in B.
+  static __device__ __forceinline__ C arg_of(const E& v, int sub) {
+    if constexpr (IsRK2<ST>::value) return sub ? v.y : v.x;
+    else { (void)sub; return Tile<DT, K>::hi_of(v); }
   }
 
   // Placement for V-fill level mp = P*L + J: left arm at positions
@@ -136,25 +148,25 @@ struct StageImpl {
       const int j = mp - P * L;
       load_coef(cf, a, ws, lane, a.lev_fill + mp + 1);
       select<0, L>(j, [&](auto J) { place<decltype(J)::value>(t, sL, sR, mp, P, lane); });
-      tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr, cf.u);
+      tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr, cf.u, cf.sub);
     }
     if (hv == H) {
       // Last level: the arms reach r points beyond the window on each side.
       // Their inner halves go to lanes 0 and 31, their outer halves become
       // the halo of lane 0 (positions -r..-1) and lane 31 (B..B+r-1).
       const int mp = H - 1;
+      load_coef(cf, a, ws, lane, a.lev_fill + H);
       C ovl[R], ovr[R];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        ovl[q] = Tile<DT, K>::hi_of(sL[mp * 2 * R + q]);
+        ovl[q] = arg_of(sL[mp * 2 * R + q], cf.sub);
         const E vl = sL[mp * 2 * R + R + q];
         if (lane == 0) t.put(q, vl);
         const E vr = sR[mp * 2 * R + q];
         if (lane == 31) t.put(K - R + q, vr);
-        ovr[q] = Tile<DT, K>::hi_of(sR[mp * 2 * R + R + q]);
+        ovr[q] = arg_of(sR[mp * 2 * R + R + q], cf.sub);
       }
-      load_coef(cf, a, ws, lane, a.lev_fill + H);
-      tile_level<ST, DT, K, true>(t, c, lane, ovl, ovr, cf.u);
+      tile_level<ST, DT, K, true>(t, c, lane, ovl, ovr, cf.u, cf.sub);
     }
   }
 
@@ -169,7 +181,7 @@ struct StageImpl {
     for (int m = 0; m < ht; ++m) {
       if (m > 0) {
         load_coef(cf, a, ws, lane, a.lev_trap + m);
-        tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr, cf.u);
+        tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr, cf.u, cf.sub);
       }
       const int P = m / L;
       const int j = m - P * L;
@@ -177,12 +189,13 @@ struct StageImpl {
     }
   }
 
-  // Copy n elements (n even, 8-byte elements, 16-byte aligned) with the warp.
+  // Copy n elements (n * sizeof(E) a multiple of 16, 16-byte aligned) with the warp.
   static __device__ __forceinline__ void warp_copy(E* __restrict__ dst, const E* __restrict__ src,
                                                    int n, int lane) {
     const uint4* s4 = reinterpret_cast<const uint4*>(src);
     uint4* d4 = reinterpret_cast<uint4*>(dst);
-    for (int i = lane; i < n / 2; i += 32) d4[i] = s4[i];
+    const int n16 = n * (int)sizeof(E) / 16;
+    for (int i = lane; i < n16; i += 32) d4[i] = s4[i];
   }
 
   static __device__ void run(const StageArgs& a, E* sm) {
@@ -224,7 +237,7 @@ struct StageImpl {
         // top of the trapezoid: level ht on [r ht, B - r ht)
         Coef cf;
         load_coef(cf, a, ws, lane, a.lev_trap + a.ht);
-        tile_level<ST, DT, K, false>(t, a.c, lane, nullptr, nullptr, cf.u);
+        tile_level<ST, DT, K, false>(t, a.c, lane, nullptr, nullptr, cf.u, cf.sub);
         const int lo = R * a.ht, hi = B - R * a.ht;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -269,7 +282,7 @@ swept_stage_kernel(const StageArgs a) {
 template <int ST, class DT, int K>
 cudaError_t launch_stage_k(const StageArgs& a, cudaStream_t s) {
   constexpr int B = 32 * K;
-  const size_t smem = stage_smem_bytes(B);
+  const size_t smem = stage_smem_bytes(B, (int)sizeof(typename DT::E));
   // set on every launch: the attribute belongs to the current device
   cudaError_t e = cudaFuncSetAttribute(swept_stage_kernel<ST, DT, K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

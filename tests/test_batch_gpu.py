@@ -70,7 +70,8 @@ def same(got, want, dtype):
 
 SMALL = [(0, 512, 1), (1, 1024, 300), (0, 2048, 255), (1, 512, 128), (0, 1536, 700),
          (1, 2560, 129), (0, 512, 0), (1, 3072, 1000), (0, 4096, 257), (1, 1024, 64),
-         (0, 1024, 511), (1, 512, 7)]
+         (0, 1024, 511), (1, 512, 7),
+         (0, 36864, 1100), (1, 18432, 777)]     # several runs of windows per stage
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
@@ -89,7 +90,7 @@ def test_batch_bit_exact(cuda_lib, dtype, bh, bk):
 def test_batch_single_block(cuda_lib, dtype):
     """One block of 4 warps: most items wait on their neighbours."""
     sw = cuda_lib
-    probs = [(0, 4096, 600), (1, 2048, 400), (0, 512, 300)]
+    probs = [(0, 4096, 600), (1, 2048, 400), (0, 512, 300), (0, 20480, 900)]
     states = [workloads.uniform(n, 50 + i) if st == 0 else 10 * workloads.ks_smoothed(n, 50 + i)
               for i, (st, n, ns) in enumerate(probs)]
     batch, out, status = run_batch(sw, probs, states, dtype, grid=1)
@@ -106,7 +107,8 @@ def test_batch_lost_message_times_out_and_gpu_stays_usable(cuda_lib):
     batch = sw.swept_batch_plan([(st, n, ns, prm(st)) for st, n, ns in probs], 1)
     info = batch.info()
     sw.swept_batch_set(batch, sw.SWEPT_BOPT_TIMEOUT_S, 0.05)
-    sw.swept_batch_set(batch, sw.SWEPT_BOPT_DROP_ITEM, info["windows"] + 3)   # a stage-1 item
+    assert info["stages"] >= 2
+    sw.swept_batch_set(batch, sw.SWEPT_BOPT_DROP_ITEM, 0)   # a stage-0 item: stage 1 waits on it
     pool = torch.tensor(build_pool(batch, states, 1), device="cuda")
     sw.swept_advance_batch(batch, pool)
     assert sw.swept_batch_status(batch) == sw.SWEPT_ETIMEOUT

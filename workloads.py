@@ -120,6 +120,14 @@ def batch_initial(kinds: np.ndarray, lengths: np.ndarray, seed: int | None = Non
     return out
 
 
+def ks_cosine(n: int = 1 << 22, dx: float = KS_DX) -> np.ndarray:
+    """The KS initial condition of the paper's Section 6 run: u(x, 0) = 2 cos(19 x / 128),
+    sampled at x_i = i * dx.  (On a periodic grid of N*dx this leaves a small jump at the
+    wrap, which the fourth-order dissipation smooths in the first steps.)"""
+    x = np.arange(n, dtype=np.float64) * dx
+    return 2.0 * np.cos(19.0 * x / 128.0)
+
+
 def ks_adjoint_state(n: int = 1 << 20, seed: int | None = None) -> np.ndarray:
     """KS initial state for the adjoint workload (same recipe as ks_smoothed)."""
     return ks_smoothed(n, seed_for(4) if seed is None else seed)
