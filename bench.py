@@ -537,14 +537,75 @@ def run_ks_rk2_workload(args):
     return 0
 
 
+def run_latency_workload(args):
+    """The latency regime of Sections 4 and 6: heat, N = 1024, r = 1/4, 2000 steps, FP64.
+
+    The per-step stepper pays one launch (the GPU's latency tau) per
+    sub-timestep; the swept advance pays one per stage of h = B/2 sub-timesteps.
+    Reports the time per sub-timestep for B in {32, ..., 1024} (stages launched
+    directly and replayed as a CUDA graph), for the naive stepper (launched and
+    graph-replayed), and the fit of Eq. 1, t(n) = n s + 2 tau / n with n = B.
+    """
+    import torch
+    import paper_1504_01380_gb300 as sw
+    from paper_1504_01380_gb300 import tune
+    n, nsteps = 1024, 2000
+    u0 = torch.tensor(workloads.heat_modes(n, 8), device="cuda")
+    u = u0.clone()
+
+    def per_sub(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            u.copy_(u0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3)
+        return best / nsteps
+
+    swept, swept_graph = {}, {}
+    for B in (32, 64, 128, 256, 512, 1024):
+        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, B)
+        swept[str(B)] = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+        swept_graph[str(B)] = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
+        plan.destroy()
+    plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, 32)
+    naive = per_sub(lambda: sw.swept_naive_advance(plan, u, nsteps), reps=3)
+    g = torch.cuda.CUDAGraph()
+    u.copy_(u0)
+    with torch.cuda.graph(g):
+        sw.swept_naive_advance(plan, u, nsteps)
+    naive_graph = per_sub(g.replay, reps=3)
+    fit = tune.fit_eq1([(int(b), t) for b, t in swept_graph.items()])
+    best = min(swept_graph, key=swept_graph.get)
+    line = {"metric": "time per sub-timestep (latency regime)", "value": swept_graph[best] * 1e9,
+            "unit": "ns per sub-timestep", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "heat1d_N1024_r0.25_2000steps_f64", "best_B": int(best)},
+            "swept_ns": {b: t * 1e9 for b, t in swept.items()},
+            "swept_graph_ns": {b: t * 1e9 for b, t in swept_graph.items()},
+            "naive_ns": naive * 1e9, "naive_graph_ns": naive_graph * 1e9,
+            "speedup_vs_naive": naive / swept_graph[best],
+            "speedup_vs_naive_graph": naive_graph / swept_graph[best],
+            "eq1_fit": {"s_ns": fit["s"] * 1e9, "tau_ns": fit["tau"] * 1e9,
+                        "n_star": fit["n_star"]} if fit else None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="heat", choices=["heat", "batch", "adjoint", "ks_rk2"],
-                    help="heat: the headline; batch / adjoint / ks_rk2: report lines for those workloads")
+    ap.add_argument("--workload", default="heat", choices=["heat", "batch", "adjoint", "ks_rk2", "latency"],
+                    help="heat: the headline; batch / adjoint / ks_rk2 / latency: report lines for those workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -554,6 +615,8 @@ def main():
         return run_adjoint_workload(args)
     if args.workload == "ks_rk2":
         return run_ks_rk2_workload(args)
+    if args.workload == "latency":
+        return run_latency_workload(args)
     return run_gpu(args)
 
 

@@ -111,10 +111,16 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        one with the triangle of the previous).
  *   SWEPT_OPT_RING_WARPS warps of a ring launch; 0 = min(resident warp slots,
  *                        N/B/2).
+ *   SWEPT_OPT_GRAPH      1: swept_advance captures its stage sequence into a
+ *                        CUDA graph on the first call for a given (u, nsteps)
+ *                        and replays it afterwards (fewer host launches: the
+ *                        GPU's counterpart of the latency tau of Section 4);
+ *                        0 (default): launch the stages directly.
  * Errors: SWEPT_EINVAL for an unknown option or value.
  */
 #define SWEPT_OPT_DIAMOND     0
 #define SWEPT_OPT_RING_WARPS  1
+#define SWEPT_OPT_GRAPH       2
 #define SWEPT_DIAMOND_AUTO    0
 #define SWEPT_DIAMOND_WINDOW  1
 #define SWEPT_DIAMOND_RING    2

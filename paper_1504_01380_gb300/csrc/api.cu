@@ -27,6 +27,11 @@ struct swept_plan_s {
   double* adj;            // adjoint scratch: work state, checkpoints, tape
   size_t adj_bytes;
   int rk2;                // two-stage Runge-Kutta: 2 levels per step, pair edges
+  int use_graph;          // replay the stage sequence as a CUDA graph
+  cudaGraphExec_t gexec;  // captured advance (valid for g_u, g_nsteps)
+  void* g_u;
+  int64_t g_nsteps;
+  int g_valid;
 };
 
 namespace {
@@ -176,6 +181,7 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
 void swept_destroy(swept_plan_t p) {
   if (!p) return;
   cudaDeviceSynchronize();
+  if (p->g_valid) cudaGraphExecDestroy(p->gexec);
   if (p->edges) cudaFree(p->edges);
   if (p->red) cudaFree(p->red);
   if (p->adj) cudaFree(p->adj);
@@ -201,13 +207,20 @@ int swept_plan_set(swept_plan_t p, int option, int64_t value) {
     p->ring_warps = (int)value;
     return SWEPT_OK;
   }
+  if (option == SWEPT_OPT_GRAPH) {
+    if (value != 0 && value != 1) return SWEPT_EINVAL;
+    p->use_graph = (int)value;
+    return SWEPT_OK;
+  }
   return SWEPT_EINVAL;
 }
 
-int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
-  if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
-  if (nsteps == 0) return SWEPT_OK;
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Enqueue the stage sequence of one advance (Section 3's stages, A5's schedule).
+int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
   const int64_t levels = p->rk2 ? 2 * nsteps : nsteps;    // sub-timesteps
   const int64_t H = p->H;
   const int64_t q = levels / H;
@@ -243,6 +256,45 @@ int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     if (e == cudaSuccess && rem > 0) e = stage(q + 1, rem, 0);
   }
   return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
+  if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
+  if (nsteps == 0) return SWEPT_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!p->use_graph) return enqueue_advance(p, u, nsteps, s);
+  // graph replay: capture the stage sequence once per (u, nsteps)
+  if (!p->g_valid || p->g_u != u || p->g_nsteps != nsteps) {
+    if (p->g_valid) {
+      cudaGraphExecDestroy(p->gexec);
+      p->g_valid = 0;
+    }
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaGraph_t g;
+    int rc = SWEPT_OK;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = enqueue_advance(p, u, nsteps, cs);
+      e = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) {
+        if (rc == SWEPT_OK) e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+      }
+    }
+    cudaStreamDestroy(cs);
+    if (rc != SWEPT_OK) return rc;
+    if (e != cudaSuccess) return cuda_status(e);
+    p->g_valid = 1;
+    p->g_u = u;
+    p->g_nsteps = nsteps;
+  }
+  return cuda_status(cudaGraphLaunch(p->gexec, s));
 }
 
 }  // extern "C"

@@ -190,16 +190,17 @@ def oracle_point(stencil, dtype, u0, x, nsteps):
 
 @pytest.mark.parametrize("dtype", [F64, F32C])
 def test_full_size_heat_2p24(cuda_lib, dtype):
-    """N = 2^24, 20000 steps, B = 512: swept == naive bit for bit, oracle samples, closed form."""
+    """N = 2^24, 20000 steps, B = 1024 (the benchmark's launch configuration): swept == naive
+    bit for bit, oracle values at sampled points, closed form."""
     sw = cuda_lib
     N, nsteps = 1 << 24, 20000
-    plan = sw.swept_plan(N, 1, HEAT, [0.25], dtype, 512)
+    plan = sw.swept_plan(N, 1, HEAT, [0.25], dtype, 1024)
     u0 = workloads.heat_noise_modes(N)
     got = run_gpu(sw, plan, u0, nsteps)
     naive = run_gpu(sw, plan, u0, nsteps, naive=True)
     assert_same(plan, got, naive)
     rng = np.random.default_rng(0)
-    for x in [0, N - 1, 511, 512] + list(rng.integers(0, N, 2)):
+    for x in [0, N - 1, 511, 512, 1023, 1024] + list(rng.integers(0, N, 2)):
         want = oracle_point(HEAT, dtype, u0, int(x), nsteps)
         if dtype == F64:
             assert got[x] == want
@@ -231,3 +232,23 @@ def test_full_size_ks_2p22(cuda_lib, dtype):
             ref = oracle_point(KS, F64, u0, x, nsteps)
             val = float(got[0][x]) + float(got[1][x])
             assert abs(val - ref) <= 1e-5 * max(abs(ref), 0.1)
+
+
+@pytest.mark.parametrize("stencil,dtype", [(HEAT, F64), (KS, F32C)])
+def test_graph_replay_bit_exact(cuda_lib, stencil, dtype):
+    """SWEPT_OPT_GRAPH: the captured stage sequence gives the same bits, twice in a row."""
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    N, B = 16 * 256, 256
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+    u0 = initial(stencil, N, 41)
+    want = oracle_run(stencil, dtype, u0, 3 * plan.h + 5)
+    import torch
+    u = to_device(sw, plan, u0)
+    for _ in range(2):
+        v = to_device(sw, plan, u0)
+        u.copy_(v)
+        sw.swept_advance(plan, u, 3 * plan.h + 5)
+        torch.cuda.synchronize()
+        assert_same(plan, from_device(plan, u), want)
