@@ -252,10 +252,13 @@ int swept_batch_plan(swept_batch_t *out, int nprob, const swept_problem_t *probs
  *                         on it time out.
  *                         -1 = none (default).
  *   SWEPT_BOPT_GRID       number of thread blocks (default: all resident).
+ *   SWEPT_BOPT_GRAPH      1 (default): replay the advance as a CUDA graph;
+ *                         0: enqueue the resets and the launch directly.
  */
 #define SWEPT_BOPT_TIMEOUT_S  0
 #define SWEPT_BOPT_DROP_ITEM  1
 #define SWEPT_BOPT_GRID       2
+#define SWEPT_BOPT_GRAPH      3
 int swept_batch_set(swept_batch_t batch, int option, double value);
 
 /* Query: items, stages, windows, grid, problems in info[0..5). */

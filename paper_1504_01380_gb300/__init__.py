@@ -35,7 +35,7 @@ EXPORTS = (
     "swept_batch_status", "swept_batch_destroy", "swept_adjoint",
 )
 
-SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID = 0, 1, 2
+SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH = 0, 1, 2, 3
 
 
 class swept_problem_t(ctypes.Structure):

@@ -253,6 +253,7 @@ struct swept_batch_s {
   int* d_status;
   double timeout_s;
   int64_t drop_item;
+  int use_graph;                // 1 (default): replay a captured graph
   // graph of one advance (memsets + the launch), rebuilt when the pool changes
   cudaGraphExec_t exec;
   void* graph_pool;
@@ -399,6 +400,7 @@ int swept_batch_plan(swept_batch_t* out, int nprob, const swept_problem_t* probs
   b->total_windows = f_off;
   b->timeout_s = 2.0;
   b->drop_item = -1;
+  b->use_graph = 1;
   cudaError_t e = cudaMalloc((void**)&b->edges, (size_t)std::max<int64_t>(e_off, 16));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->flags, (size_t)std::max<int64_t>(f_off, 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_probs, sizeof(BatchProblem) * nprob);
@@ -439,6 +441,9 @@ int swept_batch_set(swept_batch_t b, int option, double value) {
   } else if (option == SWEPT_BOPT_GRID) {
     if (value < 1 || value > 1e6) return SWEPT_EINVAL;
     b->grid = (int)value;
+  } else if (option == SWEPT_BOPT_GRAPH) {
+    if (value != 0 && value != 1) return SWEPT_EINVAL;
+    b->use_graph = (int)value;
   } else {
     return SWEPT_EINVAL;
   }
@@ -459,6 +464,7 @@ int swept_batch_info(swept_batch_t b, int64_t* info, int ninfo) {
 int swept_advance_batch(swept_batch_t b, void* pool, void* stream) {
   if (!b || !pool || ((uintptr_t)pool & 15u)) return SWEPT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!b->use_graph) return cuda_status_b(enqueue(b, pool, s));
   if (!b->graph_valid || b->graph_pool != pool) {
     if (b->graph_valid) {
       cudaGraphExecDestroy(b->exec);
