@@ -8,7 +8,10 @@ this package imports nothing from the product path.
 Contents
 --------
 * ``oracle.c`` (compiled here with gcc): per-step FP64 and FP32-compensated
-  steppers, split/merge of the compensated state, and the discrete adjoint.
+  steppers, split/merge of the compensated state, the discrete adjoint, the
+  two-stage Runge-Kutta steppers and the Euler-equations finite-volume
+  scheme (Section 7: second-order reconstruction with minmod, Roe spectral
+  radius dissipation, midpoint rule; four sub-timesteps per time step).
   These follow the definition the swept rule reorders (Sections 2-3): one
   sub-timestep applied to every point of the periodic grid, level after level.
 * ``pointwise.py``: the same sub-timestep for a single point in Python, with
@@ -75,10 +78,11 @@ def lib():
             L.oracle_adjoint_step_f64.argtypes = [i32, dp, dp, dp, dp, i64]
             L.oracle_advance_rk2_f64.argtypes = [i32, dp, dp, i64, i64, i32]
             L.oracle_rk2_substep_f64.argtypes = [i32, dp, i32, dp, dp, dp, i64]
+            L.oracle_euler_advance.argtypes = [dp, dp, i64, i64]
             for f in ("oracle_step_f64", "oracle_advance_f64", "oracle_split_f32c",
                       "oracle_merge_f32c", "oracle_step_f32c", "oracle_advance_f32c",
                       "oracle_adjoint_f64", "oracle_adjoint_step_f64", "oracle_max_threads",
-                      "oracle_advance_rk2_f64", "oracle_rk2_substep_f64"):
+                      "oracle_advance_rk2_f64", "oracle_rk2_substep_f64", "oracle_euler_advance"):
                 getattr(L, f).restype = i32
             _lib = L
         return _lib
@@ -202,6 +206,18 @@ def rk2_substep_f64(stencil: int, params, sub: int, u: np.ndarray, m: np.ndarray
     _check(lib().oracle_rk2_substep_f64(stencil, _ptr(p), int(sub), _ptr(u), _ptr(m), _ptr(out), u.size),
            "rk2_substep_f64")
     return out
+
+
+def euler_advance(params, q: np.ndarray, nsteps: int) -> np.ndarray:
+    """Euler equations (rho, m, E), shape (N, 3): nsteps RK2 steps of 4 sub-timesteps."""
+    q = np.array(q, dtype=np.float64, copy=True, order="C")
+    if q.ndim != 2 or q.shape[1] != 3:
+        raise ValueError("q must have shape (N, 3)")
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    if p.size != 3:
+        raise ValueError("Euler takes (dt, dx, gamma)")
+    _check(lib().oracle_euler_advance(_ptr(p), _ptr(q), q.shape[0], int(nsteps)), "euler_advance")
+    return q
 
 
 def max_threads() -> int:

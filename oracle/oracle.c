@@ -339,6 +339,105 @@ int oracle_rk2_substep_f64(int stencil, const double *prm, int sub, const double
     return OR_OK;
 }
 
+/* ------------------------------------------------ Euler (FP64) -------- */
+/*
+ * 1D Euler equations of gas dynamics (Section 7), q = (rho, m = rho u, E),
+ * p = (gamma - 1)(E - m^2/(2 rho)).  Second-order finite volumes (Section 2:
+ * a gradient sub-timestep, then a flux-and-update sub-timestep), minmod
+ * limiter, interface flux with scalar dissipation equal to the spectral
+ * radius of the Roe matrix, midpoint Runge-Kutta: four sub-timesteps of
+ * radius 1 per time step (Section 2's count):
+ *   G  : s_i = minmod(q_i - q_{i-1}, q_{i+1} - q_i) per component
+ *   F_a: q'_i = q_i - a (dt/dx) (F_{i+1/2} - F_{i-1/2}),  a = 1/2, then 1
+ *   step: (G on q, F_{1/2} -> q_mid, G on q_mid, F_1 from q_mid's fluxes on q)
+ * Canonical evaluation (every operation IEEE round-to-nearest; / and sqrt
+ * correctly rounded):
+ *   minmod(a, b) = (a > 0 && b > 0) ? fmin(a, b) : (a < 0 && b < 0) ? fmax(a, b) : 0
+ *   face i+1/2: qL = fma(0.5, s_i, q_i), qR = fma(-0.5, s_{i+1}, q_{i+1})
+ *   state (rho, m, E): u = m / rho; p = g1 * (E - 0.5 * (m * u)); H = (E + p) / rho
+ *   f(q) = (m, fma(m, u, p), (E + p) * u)
+ *   Roe: sl = sqrt(rho_L), sr = sqrt(rho_R), d = sl + sr,
+ *        ut = (sl*u_L + sr*u_R) / d, Ht = (sl*H_L + sr*H_R) / d,
+ *        c2 = g1 * (Ht - 0.5 * (ut * ut)), lam = |ut| + sqrt(fmax(c2, 0))
+ *   F_k = 0.5 * ((fL_k + fR_k) - lam * (qR_k - qL_k))
+ *   q'_k = fma(-ca, F_{i+1/2,k} - F_{i-1/2,k}, q_k),  ca = a * (dt / dx)
+ * with g1 = gamma - 1; params = {dt, dx, gamma}.
+ */
+static inline double minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return fmin(a, b);
+    if (a < 0.0 && b < 0.0) return fmax(a, b);
+    return 0.0;
+}
+
+static void euler_face_flux(const double *qL, const double *qR, double g1, double *F)
+{
+    double uL = qL[1] / qL[0], uR = qR[1] / qR[0];
+    double pL = g1 * (qL[2] - 0.5 * (qL[1] * uL));
+    double pR = g1 * (qR[2] - 0.5 * (qR[1] * uR));
+    double HL = (qL[2] + pL) / qL[0], HR = (qR[2] + pR) / qR[0];
+    double fL[3] = {qL[1], fma(qL[1], uL, pL), (qL[2] + pL) * uL};
+    double fR[3] = {qR[1], fma(qR[1], uR, pR), (qR[2] + pR) * uR};
+    double sl = sqrt(qL[0]), sr = sqrt(qR[0]);
+    double d = sl + sr;
+    double ut = (sl * uL + sr * uR) / d;
+    double Ht = (sl * HL + sr * HR) / d;
+    double c2 = g1 * (Ht - 0.5 * (ut * ut));
+    double lam = fabs(ut) + sqrt(fmax(c2, 0.0));
+    for (int k = 0; k < 3; ++k) F[k] = 0.5 * ((fL[k] + fR[k]) - lam * (qR[k] - qL[k]));
+}
+
+/* q, s: arrays of 3n (component-major per point: q[3i+k]). */
+static void euler_slopes(const double *q, double *s, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t im = wrap(i - 1, n), ip = wrap(i + 1, n);
+        for (int k = 0; k < 3; ++k)
+            s[3 * i + k] = minmod(q[3 * i + k] - q[3 * im + k], q[3 * ip + k] - q[3 * i + k]);
+    }
+}
+
+/* out = base - ca * (F_{i+1/2} - F_{i-1/2}), fluxes from (q, s). */
+static void euler_update(const double *q, const double *s, const double *base, double ca, double g1,
+                         double *out, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double Fl[3], Fr[3], qL[3], qR[3];
+        int64_t im = wrap(i - 1, n), ip = wrap(i + 1, n);
+        for (int k = 0; k < 3; ++k) {
+            qL[k] = fma(0.5, s[3 * im + k], q[3 * im + k]);
+            qR[k] = fma(-0.5, s[3 * i + k], q[3 * i + k]);
+        }
+        euler_face_flux(qL, qR, g1, Fl);
+        for (int k = 0; k < 3; ++k) {
+            qL[k] = fma(0.5, s[3 * i + k], q[3 * i + k]);
+            qR[k] = fma(-0.5, s[3 * ip + k], q[3 * ip + k]);
+        }
+        euler_face_flux(qL, qR, g1, Fr);
+        for (int k = 0; k < 3; ++k) out[3 * i + k] = fma(-ca, Fr[k] - Fl[k], base[3 * i + k]);
+    }
+}
+
+/* q (3n values, point-major) <- q after nsteps RK2 time steps (4 sub-timesteps each). */
+int oracle_euler_advance(const double *prm, double *q, int64_t n, int64_t nsteps)
+{
+    if (n <= 0 || nsteps < 0 || !(prm[1] > 0.0)) return OR_EINVAL;
+    double dtdx = prm[0] / prm[1], g1 = prm[2] - 1.0;
+    double *s = (double *)malloc((size_t)3 * n * sizeof(double));
+    double *qm = (double *)malloc((size_t)3 * n * sizeof(double));
+    double *qn = (double *)malloc((size_t)3 * n * sizeof(double));
+    if (!s || !qm || !qn) { free(s); free(qm); free(qn); return OR_ENOMEM; }
+    for (int64_t t = 0; t < nsteps; ++t) {
+        euler_slopes(q, s, n);
+        euler_update(q, s, q, 0.5 * dtdx, g1, qm, n);
+        euler_slopes(qm, s, n);
+        euler_update(qm, s, q, 1.0 * dtdx, g1, qn, n);
+        memcpy(q, qn, (size_t)3 * n * sizeof(double));
+    }
+    free(s); free(qm); free(qn);
+    return OR_OK;
+}
+
 /* ------------------------------------------------------- adjoint ------ */
 
 /*

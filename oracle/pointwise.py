@@ -10,6 +10,7 @@ fma independent of the C library.
 """
 from __future__ import annotations
 
+import math
 from fractions import Fraction
 
 
@@ -43,6 +44,34 @@ def ks_point(v, a: float, b: float, e: float) -> float:
     return fma(e, D, fma(b, w0, fma(a, t, v[2])))
 
 
+EULER = 4
+
+
+def _minmod(a: float, b: float) -> float:
+    if a > 0.0 and b > 0.0:
+        return min(a, b)
+    if a < 0.0 and b < 0.0:
+        return max(a, b)
+    return 0.0
+
+
+def euler_face_flux(qL, qR, g1: float):
+    """Interface flux with Roe-spectral-radius dissipation (order as in oracle.c)."""
+    uL, uR = qL[1] / qL[0], qR[1] / qR[0]
+    pL = g1 * (qL[2] - 0.5 * (qL[1] * uL))
+    pR = g1 * (qR[2] - 0.5 * (qR[1] * uR))
+    HL, HR = (qL[2] + pL) / qL[0], (qR[2] + pR) / qR[0]
+    fL = (qL[1], fma(qL[1], uL, pL), (qL[2] + pL) * uL)
+    fR = (qR[1], fma(qR[1], uR, pR), (qR[2] + pR) * uR)
+    sl, sr = math.sqrt(qL[0]), math.sqrt(qR[0])
+    d = sl + sr
+    ut = (sl * uL + sr * uR) / d
+    Ht = (sl * HL + sr * HR) / d
+    c2 = g1 * (Ht - 0.5 * (ut * ut))
+    lam = abs(ut) + math.sqrt(max(c2, 0.0))
+    return tuple(0.5 * ((fL[k] + fR[k]) - lam * (qR[k] - qL[k])) for k in range(3))
+
+
 def make_point_update(stencil: int, params):
     """Return (radius, f) with f(values at i-r..i+r of level t, t) -> value at i of level t+1.
 
@@ -51,7 +80,10 @@ def make_point_update(stencil: int, params):
     variable): values are pairs (u, m); even levels take sub-timestep A,
     (u, m) -> (u, u + dt/2 f(u)), odd levels sub-timestep B,
     (u, m) -> (u + dt f(m), m).  The second component after B is carried
-    along unchanged and never read.
+    along unchanged and never read.  Euler equations (stencil 4, Section 7):
+    values are 9-tuples (q, q_mid, slopes) of conserved variables; level t
+    takes sub-timestep t mod 4 (slopes of q, half-step flux update into
+    q_mid, slopes of q_mid, full-step flux update of q from q_mid's fluxes).
     """
     if stencil == 0:
         r = float(params[0])
@@ -88,4 +120,27 @@ def make_point_update(stencil: int, params):
             tt = Gp - Gm
             return (fma(e, D, fma(b, w0, fma(a, tt, u0))), x[2])
         return 2, ks_rk2
+    if stencil == EULER:
+        dtdx, g1 = params[0] / params[1], params[2] - 1.0
+
+        def euler(v, t):
+            # state per point: (q0, q1, q2, qm0, qm1, qm2, s0, s1, s2)
+            sub = t % 4
+            c = v[1]
+            if sub in (0, 2):                      # slopes of q (0) or of the midpoint (2)
+                o = 0 if sub == 0 else 3
+                sl = tuple(_minmod(c[o + k] - v[0][o + k], v[2][o + k] - c[o + k]) for k in range(3))
+                return c[:6] + sl
+            o = 0 if sub == 1 else 3                 # fluxes from q (1) or the midpoint (3)
+            def face(a, b):
+                qL = tuple(fma(0.5, a[6 + k], a[o + k]) for k in range(3))
+                qR = tuple(fma(-0.5, b[6 + k], b[o + k]) for k in range(3))
+                return euler_face_flux(qL, qR, g1)
+            Fl, Fr = face(v[0], c), face(c, v[2])
+            ca = (0.5 if sub == 1 else 1.0) * dtdx
+            new = tuple(fma(-ca, Fr[k] - Fl[k], c[k]) for k in range(3))
+            if sub == 1:
+                return c[:3] + new + c[6:]
+            return new + c[3:]
+        return 1, euler
     raise ValueError(f"unknown stencil {stencil}")

@@ -64,10 +64,16 @@ def swept_simulate(stencil: int, params, u0, P: int, nsteps: int, max_stages: in
     # store[j]: (x, t) -> (value, origin); origin 'own' or ('recv', stage)
     store = [dict() for _ in range(P)]
     pair = stencil in (2, 3)            # two-stage Runge-Kutta: (u, m) per point
+    euler = stencil == 4                # Euler: (q, q_mid, slopes), q = u0[x] (3 values)
     for j in range(P):
         for x in range(j * B, (j + 1) * B):
-            v0 = float(u0[x])
-            store[j][(x, 0)] = ((v0, v0) if pair else v0, "own")
+            if euler:
+                q = tuple(float(c) for c in u0[x])
+                v = q + q + (0.0, 0.0, 0.0)
+            else:
+                v0 = float(u0[x])
+                v = (v0, v0) if pair else v0
+            store[j][(x, 0)] = (v, "own")
     count: dict = {}
     trace = SweptTrace(u_final=[], compute_count=count, stages=0)
 
@@ -141,6 +147,6 @@ def swept_simulate(stencil: int, params, u0, P: int, nsteps: int, max_stages: in
     for j in range(P):
         for (x, t), (v, _) in store[j].items():
             if t == nsteps and final[x] is None:
-                final[x] = v[0] if pair else v
+                final[x] = v[0] if pair else (v[:3] if euler else v)
     trace.u_final = final
     return trace

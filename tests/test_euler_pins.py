@@ -1,0 +1,155 @@
+"""Pins of the Euler-equations oracle (Section 7's scheme; readings stated in oracle.c).
+
+Conservation of mass, momentum and energy; exact preservation of a uniform state;
+mirror symmetry; the periodic Sod problem against the exact Riemann solution (an
+independent solver written here from the Riemann problem's wave relations) with
+error decreasing under refinement; and the swept stages reproducing per-step
+stepping bit for bit.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.swept_bruteforce import swept_simulate
+
+GAMMA = 1.4
+
+
+def sod_periodic(n):
+    """Cells on [0, 1): rho, u, p = (0.125, 0, 0.1) on the left half, (1, 0, 1) on the right."""
+    x = (np.arange(n) + 0.5) / n
+    left = x < 0.5
+    rho = np.where(left, 0.125, 1.0)
+    p = np.where(left, 0.1, 1.0)
+    q = np.zeros((n, 3))
+    q[:, 0] = rho
+    q[:, 2] = p / (GAMMA - 1.0)
+    return x, q
+
+
+def prim(q):
+    rho = q[:, 0]
+    u = q[:, 1] / rho
+    p = (GAMMA - 1.0) * (q[:, 2] - 0.5 * rho * u * u)
+    return rho, u, p
+
+
+def exact_riemann(rl, ul, pl, rr, ur, pr, xi, g=GAMMA):
+    """Density of the exact Riemann solution at similarity coordinates xi = (x - x0)/t."""
+    from scipy.optimize import brentq
+    cl, cr = math.sqrt(g * pl / rl), math.sqrt(g * pr / rr)
+
+    def f(p, rk, pk, ck):
+        if p > pk:                                    # shock
+            A, Bk = 2 / ((g + 1) * rk), (g - 1) / (g + 1) * pk
+            return (p - pk) * math.sqrt(A / (p + Bk))
+        return 2 * ck / (g - 1) * ((p / pk) ** ((g - 1) / (2 * g)) - 1)   # rarefaction
+
+    ps = brentq(lambda p: f(p, rl, pl, cl) + f(p, rr, pr, cr) + (ur - ul), 1e-12, 100.0, xtol=1e-15)
+    us = 0.5 * (ul + ur) + 0.5 * (f(ps, rr, pr, cr) - f(ps, rl, pl, cl))
+
+    def side(rk, pk, ck, uk, sgn):
+        # density of the star region on this side and the wave description
+        if ps > pk:
+            rs = rk * ((ps / pk + (g - 1) / (g + 1)) / ((g - 1) / (g + 1) * ps / pk + 1))
+            S = uk + sgn * ck * math.sqrt((g + 1) / (2 * g) * ps / pk + (g - 1) / (2 * g))
+            return rs, ("shock", S)
+        rs = rk * (ps / pk) ** (1 / g)
+        cs = ck * (ps / pk) ** ((g - 1) / (2 * g))
+        return rs, ("fan", uk + sgn * ck, us + sgn * cs)
+
+    rsl, wl = side(rl, pl, cl, ul, -1)
+    rsr, wr = side(rr, pr, cr, ur, +1)
+    out = np.empty_like(xi)
+    for i, s in enumerate(xi):
+        if s <= us:                                   # left of the contact
+            if wl[0] == "shock":
+                out[i] = rl if s < wl[1] else rsl
+            elif s <= wl[1]:
+                out[i] = rl
+            elif s >= wl[2]:
+                out[i] = rsl
+            else:                                     # inside the left fan
+                c = 2 / (g + 1) * (cl + (g - 1) / 2 * (ul - s))
+                out[i] = rl * (c / cl) ** (2 / (g - 1))
+        else:
+            if wr[0] == "shock":
+                out[i] = rr if s > wr[1] else rsr
+            elif s >= wr[1]:
+                out[i] = rr
+            elif s <= wr[2]:
+                out[i] = rsr
+            else:
+                c = 2 / (g + 1) * (cr - (g - 1) / 2 * (ur - s))
+                out[i] = rr * (c / cr) ** (2 / (g - 1))
+    return out
+
+
+def sod_exact_density(x, t):
+    """Two Riemann problems on the periodic domain: at x = 1/2 (low | high) and at x = 0 (high | low)."""
+    rho = np.empty_like(x)
+    mid = (x > 0.25) & (x < 0.75)
+    rho[mid] = exact_riemann(0.125, 0.0, 0.1, 1.0, 0.0, 1.0, (x[mid] - 0.5) / t)
+    xw = np.where(x < 0.5, x, x - 1.0)[~mid]
+    rho[~mid] = exact_riemann(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, xw / t)
+    return rho
+
+
+@pytest.mark.parametrize("n", [64, 200])
+def test_conservation(n):
+    x, q = sod_periodic(n)
+    out = oracle.euler_advance([0.2 / n, 1.0 / n, GAMMA], q, 150)
+    for k in range(3):
+        scale = math.fsum(np.abs(q[:, k])) + 1.0
+        assert abs(math.fsum(out[:, k]) - math.fsum(q[:, k])) <= 1e-12 * scale
+
+
+def test_uniform_state_is_fixed_exactly():
+    q = np.tile([0.7, 0.35, 2.5], (40, 1))
+    assert np.array_equal(oracle.euler_advance([0.001, 0.02, GAMMA], q, 50), q)
+
+
+def test_mirror_symmetry():
+    """(rho, m, E)(x) -> (rho, -m, E)(-x) maps solutions to solutions."""
+    n = 128
+    x, q = sod_periodic(n)
+    q[:, 1] = 0.3 * np.sin(2 * np.pi * x)
+    q[:, 2] += 0.5 * q[:, 1] ** 2 / q[:, 0]
+    a = oracle.euler_advance([0.2 / n, 1.0 / n, GAMMA], q, 60)
+    qm = q[::-1].copy()
+    qm[:, 1] *= -1
+    b = oracle.euler_advance([0.2 / n, 1.0 / n, GAMMA], qm, 60)[::-1]
+    b[:, 1] *= -1
+    assert np.max(np.abs(a - b)) <= 1e-13
+
+
+def test_sod_against_exact_riemann_and_converges():
+    t = 0.1
+    errs = []
+    for n in (200, 800):
+        x, q = sod_periodic(n)
+        dt = 0.2 / n                                   # CFL ~ 0.2 * max(|u| + c) ~ 0.4
+        steps = int(round(t / dt))
+        out = oracle.euler_advance([dt, 1.0 / n, GAMMA], q, steps)
+        rho, u, p = prim(out)
+        assert np.all(rho > 0) and np.all(p > 0)
+        errs.append(np.mean(np.abs(rho - sod_exact_density(x, steps * dt))))
+    assert errs[0] < 0.02
+    assert errs[1] < 0.6 * errs[0]                    # refinement by 4 at least halves the error
+
+
+@pytest.mark.parametrize("B", [4, 8])
+@pytest.mark.parametrize("nsteps", [1, 2, 5])
+def test_euler_swept_bruteforce_matches_per_step(B, nsteps):
+    n = 16
+    x, q = sod_periodic(n)
+    q[:, 1] = 0.1 * np.cos(2 * np.pi * x)
+    prm = [0.2 / n, 1.0 / n, GAMMA]
+    tr = swept_simulate(4, prm, q, n // B, 4 * nsteps)
+    got = np.array(tr.u_final)
+    assert np.array_equal(got, oracle.euler_advance(prm, q, nsteps))
+    assert all(c == 1 for c in tr.compute_count.values())
