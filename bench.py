@@ -598,14 +598,98 @@ def run_latency_workload(args):
     return 0
 
 
+def euler_state(n: int, cfl: float = 0.2):
+    """Periodic Sod state of Section 7 (rho, u, p = 0.125, 0, 0.1 | 1, 0, 1) on [0, 1), gamma 1.4,
+    as planar rho/m/E; dt = cfl * dx."""
+    import numpy as np
+    x = (np.arange(n) + 0.5) / n
+    left = x < 0.5
+    rho = np.where(left, 0.125, 1.0)
+    E = np.where(left, 0.1, 1.0) / 0.4
+    dx = 1.0 / n
+    return np.concatenate([rho, np.zeros(n), E]), [cfl * dx, dx, 1.4]
+
+
+def run_euler_workload(args):
+    """Euler equations (Section 7): second-order finite volumes, minmod, Roe spectral-radius
+    dissipation, midpoint rule (4 sub-timesteps per step), FP64, periodic Sod state.
+
+    Throughput at N = 2^23 cells (201 MB of state, larger than L2) for B = 32, 64, 128 against
+    the naive stepper (two fused launches per step); and the latency regime at N = 4096 cells
+    (the paper's run had about 50 cells on each of 64 ranks): time per sub-timestep, swept
+    (graph-replayed stages) against naive (graph-replayed launches).
+    """
+    import torch
+    import paper_1504_01380_gb300 as sw
+    n, nsteps = 1 << 23, 40
+    q0, prm = euler_state(n)
+    u0 = torch.tensor(q0, device="cuda")
+    u = u0.clone()
+
+    def best_time(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            u.copy_(u0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return sum(ts) / len(ts)
+
+    res = {}
+    for B in (32, 64, 128):
+        plan = sw.swept_plan(n, 1, sw.SWEPT_EULER, prm, sw.SWEPT_F64, B)
+        res[str(B)] = n * nsteps / best_time(lambda: sw.swept_advance(plan, u, nsteps), args.steps)
+        plan.destroy()
+    plan = sw.swept_plan(n, 1, sw.SWEPT_EULER, prm, sw.SWEPT_F64, 64)
+    naive = n * nsteps / best_time(lambda: sw.swept_naive_advance(plan, u, nsteps), args.steps)
+    plan.destroy()
+
+    # latency regime
+    nl, stl = 4096, 500
+    ql, prml = euler_state(nl)
+    u0 = torch.tensor(ql, device="cuda")
+    u = u0.clone()
+    lat = {}
+    for B in (32, 64, 128):
+        plan = sw.swept_plan(nl, 1, sw.SWEPT_EULER, prml, sw.SWEPT_F64, B)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+        lat[str(B)] = best_time(lambda: sw.swept_advance(plan, u, stl), 3) / (4 * stl)
+        plan.destroy()
+    plan = sw.swept_plan(nl, 1, sw.SWEPT_EULER, prml, sw.SWEPT_F64, 32)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        sw.swept_naive_advance(plan, u, stl)
+    naive_lat = best_time(g.replay, 3) / (4 * stl)
+    best = max(res, key=res.get)
+    bl = min(lat, key=lat.get)
+    line = {"metric": METRIC, "value": res[best], "unit": UNIT + " (time steps of 4 sub-timesteps)",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": n * nsteps / res[best] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"euler1d_sod_periodic_N{n}_{nsteps}steps_f64_gamma1.4_cfl0.2",
+                       "B": int(best)},
+            "tile_sweep": res, "naive": naive, "swept_over_naive": res[best] / naive,
+            "latency": {"workload": f"euler1d_sod_periodic_N{nl}_{stl}steps", "best_B": int(bl),
+                        "swept_graph_ns_per_sub": {b: t * 1e9 for b, t in lat.items()},
+                        "naive_graph_ns_per_sub": naive_lat * 1e9,
+                        "speedup_vs_naive": naive_lat / lat[bl]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="heat", choices=["heat", "batch", "adjoint", "ks_rk2", "latency"],
-                    help="heat: the headline; batch / adjoint / ks_rk2 / latency: report lines for those workloads")
+    ap.add_argument("--workload", default="heat",
+                    choices=["heat", "batch", "adjoint", "ks_rk2", "latency", "euler"],
+                    help="heat: the headline; the others print report lines for those workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -617,6 +701,8 @@ def main():
         return run_ks_rk2_workload(args)
     if args.workload == "latency":
         return run_latency_workload(args)
+    if args.workload == "euler":
+        return run_euler_workload(args)
     return run_gpu(args)
 
 

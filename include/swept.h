@@ -23,6 +23,8 @@
  *   SWEPT_F64  : double u[N].
  *   SWEPT_F32C : float hi[N] followed by float lo[N] (8N bytes); the value
  *                of point i is hi[i] + lo[i] (compensated FP32).
+ *   SWEPT_EULER plans (FP64): double rho[N], then m[N], then E[N] (24N
+ *                bytes; the conserved variables density, momentum, energy).
  */
 #ifndef SWEPT_H
 #define SWEPT_H
@@ -55,6 +57,16 @@ extern "C" {
  * and in the edge buffers.  Same parameters as the forward-Euler stencils. */
 #define SWEPT_HEAT_RK2  2
 #define SWEPT_KS_RK2    3
+/* Euler equations of gas dynamics (Section 7), FP64 only, radius 1:
+ * q = (rho, m, E), p = (gamma - 1)(E - m^2/(2 rho)); second-order finite
+ * volumes with minmod-limited slopes, interface flux = mean physical flux
+ * minus the spectral radius of the Roe matrix times the jump, midpoint rule.
+ * One time step is four sub-timesteps (Section 2): slopes of q, half-step
+ * flux update into q_mid, slopes of q_mid, full-step flux update of q with
+ * q_mid's fluxes.  nsteps counts time steps.  params = {dt, dx, gamma}
+ * (nparams = 3, dx > 0, dt >= 0, gamma > 1).  B in {32, 64, 128}; 9-value
+ * point states (72 bytes) exist on chip and in the edge buffers. */
+#define SWEPT_EULER     4
 
 /* Status codes. */
 #define SWEPT_OK         0
@@ -83,13 +95,14 @@ typedef struct swept_plan_s *swept_plan_t;
  * (radius `radius`, parameters `params[0..nparams)`) in arithmetic `dtype`.
  *   N       >= B, N % B == 0.
  *   radius  must equal the stencil's radius (1 heat, 2 KS, either time
- *           integrator).
+ *           integrator; 1 Euler equations).
  *   B       tile width: 32*K points with K in {1,2,4,8,16,32}, K % radius
  *           == 0 (Section 3 asks for an even number of points per node; in
  *           general B % (2*radius) == 0).  B = 0 picks the tuned default.
  *   params  host pointer; copied.
  * Allocates the edge double-buffer (2 * 2N values, 32N bytes; 64N for the
- * Runge-Kutta pairs) on the current device.  *out is set on success.
+ * Runge-Kutta pairs; 288N for Euler point states) on the current device.
+ * *out is set on success.
  * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP, SWEPT_ENOMEM, SWEPT_ECUDA.
  */
 int swept_plan(swept_plan_t *out, int64_t N, int radius, int stencil_id,
@@ -149,7 +162,9 @@ int swept_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream);
  * swept_naive_advance -- the same result by per-step stepping: one kernel
  * launch and one full read and write of u per sub-timestep (the "straight"
  * decomposition that Section 6 compares against).  Uses the plan's scratch
- * as the second buffer.  Same arguments and errors as swept_advance.
+ * as the second buffer.  Euler plans take two launches per time step (each
+ * fuses a slope sub-timestep with the flux sub-timestep that follows it).
+ * Same arguments and errors as swept_advance.
  */
 int swept_naive_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream);
 
@@ -172,8 +187,8 @@ int swept_naive_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream
  *   u0, lambda_T, grad_u0  device double[N]; grad_u0 may not alias u0.
  * Scratch (plan-owned, grown on demand): (1 + segments + 2*K_cycles*h) * 8N
  * bytes for KS; none for heat.
- * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP (F32C or Runge-Kutta plan), SWEPT_ENOMEM,
- * SWEPT_ECUDA.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP (F32C, Runge-Kutta or Euler plan),
+ * SWEPT_ENOMEM, SWEPT_ECUDA.
  */
 int swept_adjoint(swept_plan_t plan, const void *u0, const void *lambda_T, void *grad_u0,
                   int64_t nsteps, int K_cycles, void *stream);
@@ -196,7 +211,8 @@ int swept_f32c_merge(int64_t N, const void *u32c, double *u64, void *stream);
  * or the directional derivative <u, v>).  Compensated (TwoSum/TwoProd)
  * accumulation in a fixed order, so repeated calls give identical bits.
  *   u    device state in the plan's layout (F32C values enter as
- *        fl64(hi + lo)).
+ *        fl64(hi + lo)); for an Euler plan, any one N-value block (pass
+ *        u + N for the momentum, u + 2N for the energy).
  *   what SWEPT_SUM, SWEPT_HALF_SUMSQ or SWEPT_DOT.
  *   v    device double[N] for SWEPT_DOT, else ignored.
  *   out  device double[1]: the result is written there (no host sync).

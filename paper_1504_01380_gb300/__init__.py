@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
 
 SWEPT_F64, SWEPT_F32C = 0, 1
-SWEPT_HEAT, SWEPT_KS, SWEPT_HEAT_RK2, SWEPT_KS_RK2 = 0, 1, 2, 3
+SWEPT_HEAT, SWEPT_KS, SWEPT_HEAT_RK2, SWEPT_KS_RK2, SWEPT_EULER = 0, 1, 2, 3, 4
 SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT = 0, 1, 2
 SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP = 0, -1, -2, -3, -4, -5
 SWEPT_ETOOBIG = -6
@@ -24,7 +24,7 @@ SWEPT_NOALLOC_MAX_N = 1 << 20
 SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS, SWEPT_OPT_GRAPH = 0, 1, 2
 SWEPT_DIAMOND_AUTO, SWEPT_DIAMOND_WINDOW, SWEPT_DIAMOND_RING = 0, 1, 2
 
-RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2, SWEPT_HEAT_RK2: 1, SWEPT_KS_RK2: 2}
+RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2, SWEPT_HEAT_RK2: 1, SWEPT_KS_RK2: 2, SWEPT_EULER: 1}
 
 # Every entry point declared in include/swept.h.
 EXPORTS = (
@@ -156,7 +156,7 @@ class Plan:
 
     @property
     def state_bytes(self) -> int:
-        return 8 * self.N
+        return (24 if self.stencil == SWEPT_EULER else 8) * self.N
 
     def destroy(self):
         if self._h is not None:
@@ -188,7 +188,11 @@ def swept_plan_set(plan: Plan, option: int, value: int) -> Plan:
 
 
 def swept_advance(plan: Plan, u, nsteps: int, stream=None):
-    """u <- u after nsteps sub-timesteps (swept rule), in place on ``stream``."""
+    """u <- u after nsteps time steps (swept rule), in place on ``stream``.
+
+    A time step is one sub-timestep for the forward-Euler stencils, two for the
+    Runge-Kutta ones and four for the Euler equations (state: rho, m, E blocks).
+    """
     _check(load().swept_advance(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(nsteps),
                                 _stream(stream)), "swept_advance")
     return u
@@ -231,7 +235,7 @@ def swept_reduce(plan: Plan, u, what: int, v=None, out=None, stream=None):
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=u.device)
     vp = _dev_ptr(v, 8 * plan.N, "v") if v is not None else ctypes.c_void_p(0)
-    _check(load().swept_reduce(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(what), vp,
+    _check(load().swept_reduce(plan.handle, _dev_ptr(u, 8 * plan.N, "u"), int(what), vp,
                                _dev_ptr(out, 8, "out"), _stream(stream)), "swept_reduce")
     return out
 

@@ -17,9 +17,9 @@ using swept::StageArgs;
 struct swept_plan_s {
   int64_t N;
   int radius, stencil, dtype, B, K, H, nwin, device;
-  double prm[2];
+  double prm[3];
   Consts c;
-  unsigned char* edges;   // two buffers of nwin * 2B elements of 8 bytes
+  unsigned char* edges;   // two buffers of nwin * 2B edge elements
   size_t edge_half;       // bytes per buffer
   double* red;            // 2 * kReduceBlocks partials
   int diamond;            // SWEPT_DIAMOND_*
@@ -27,6 +27,7 @@ struct swept_plan_s {
   double* adj;            // adjoint scratch: work state, checkpoints, tape
   size_t adj_bytes;
   int rk2;                // two-stage Runge-Kutta: 2 levels per step, pair edges
+  int subs;               // sub-timesteps (levels) per time step: 1, 2 or 4
   int use_graph;          // replay the stage sequence as a CUDA graph
   cudaGraphExec_t gexec;  // captured advance (valid for g_u, g_nsteps)
   void* g_u;
@@ -47,6 +48,13 @@ int cuda_status(cudaError_t e) {
 // the FP64 values rounded to nearest.
 int make_consts(int stencil, const double* p, int np, Consts& c) {
   std::memset(&c, 0, sizeof c);
+  if (stencil == SWEPT_EULER) {
+    // dt/dx and gamma - 1, FP64 in this order; params = {dt, dx, gamma}
+    if (np < 3 || !(p[1] > 0.0) || !(p[0] >= 0.0) || !(p[2] > 1.0)) return SWEPT_EINVAL;
+    c.dtdx = p[0] / p[1];
+    c.g1 = p[2] - 1.0;
+    return SWEPT_OK;
+  }
   if (stencil == SWEPT_HEAT_RK2 || stencil == SWEPT_KS_RK2) stencil -= 2;   // same constants
   if (stencil == SWEPT_HEAT) {
     if (np < 1) return SWEPT_EINVAL;
@@ -72,6 +80,7 @@ int make_consts(int stencil, const double* p, int np, Consts& c) {
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
+  if (p->stencil == SWEPT_EULER) return swept::launch_stage_euler_f64(p->K, a, s);
   if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_stage_heatrk2_f64(p->K, a, s);
   if (p->stencil == SWEPT_KS_RK2) return swept::launch_stage_ksrk2_f64(p->K, a, s);
   if (p->stencil == SWEPT_HEAT)
@@ -82,6 +91,7 @@ cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t
 }
 
 cudaError_t launch_ring(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
+  if (p->stencil == SWEPT_EULER) return swept::launch_ring_euler_f64(p->K, a, p->ring_warps, s);
   if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_ring_heatrk2_f64(p->K, a, p->ring_warps, s);
   if (p->stencil == SWEPT_KS_RK2) return swept::launch_ring_ksrk2_f64(p->K, a, p->ring_warps, s);
   if (p->stencil == SWEPT_HEAT)
@@ -99,10 +109,10 @@ bool use_ring(const swept_plan_s* p) {
   return p->nwin >= 8;
 }
 
-// Default tile width: the largest of 512, 256, ... that divides N and keeps
-// K a multiple of the radius.
-int default_B(int64_t N, int radius) {
-  for (int K = 16; K >= 1; K /= 2) {
+// Default tile width: the largest of 512, 256, ... (64, 32 for the Euler
+// equations) that divides N and keeps K a multiple of the radius.
+int default_B(int64_t N, int radius, int stencil) {
+  for (int K = stencil == SWEPT_EULER ? 2 : 16; K >= 1; K /= 2) {
     const int B = 32 * K;
     if (K % radius == 0 && N % B == 0) return B;
   }
@@ -132,17 +142,19 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
                int nparams, int dtype, int B) {
   if (!out || !params) return SWEPT_EINVAL;
   *out = nullptr;
-  if (stencil_id < SWEPT_HEAT || stencil_id > SWEPT_KS_RK2) return SWEPT_EINVAL;
-  const int rad = (stencil_id == SWEPT_HEAT || stencil_id == SWEPT_HEAT_RK2) ? 1 : 2;
+  if (stencil_id < SWEPT_HEAT || stencil_id > SWEPT_EULER) return SWEPT_EINVAL;
+  const bool euler = stencil_id == SWEPT_EULER;
+  const int rad = (stencil_id == SWEPT_HEAT || stencil_id == SWEPT_HEAT_RK2 || euler) ? 1 : 2;
   if (radius != rad) return SWEPT_EINVAL;
   if (dtype != SWEPT_F64 && dtype != SWEPT_F32C) return SWEPT_EINVAL;
-  const bool rk2 = stencil_id >= SWEPT_HEAT_RK2;
-  if (rk2 && dtype != SWEPT_F64) return SWEPT_ENOTSUP;
+  const bool rk2 = stencil_id == SWEPT_HEAT_RK2 || stencil_id == SWEPT_KS_RK2;
+  if ((rk2 || euler) && dtype != SWEPT_F64) return SWEPT_ENOTSUP;
   if (N <= 0) return SWEPT_EINVAL;
-  if (B == 0) B = default_B(N, rad);
+  if (B == 0) B = default_B(N, rad, stencil_id);
   if (B <= 0 || B % 32) return SWEPT_EINVAL;
   const int K = B / 32;
   if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32) return SWEPT_ENOTSUP;
+  if (euler && K > 4) return SWEPT_ENOTSUP;
   if (K % rad) return SWEPT_EINVAL;
   if (N % B) return SWEPT_EINVAL;
   if (N / B > (int64_t)0x7fffffff) return SWEPT_EINVAL;
@@ -160,12 +172,13 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->K = K;
   p->H = B / (2 * rad);
   p->nwin = (int)(N / B);
-  p->prm[0] = params[0];
-  p->prm[1] = nparams > 1 ? params[1] : 0.0;
+  for (int i = 0; i < 3; ++i) p->prm[i] = i < nparams ? params[i] : 0.0;
   p->c = c;
   p->rk2 = rk2 ? 1 : 0;
+  p->subs = euler ? 4 : (rk2 ? 2 : 1);
   cudaGetDevice(&p->device);
-  p->edge_half = (size_t)p->nwin * 2 * B * (rk2 ? 16 : 8);
+  const size_t esize = euler ? sizeof(swept::EulerE) : (rk2 ? 16 : 8);
+  p->edge_half = (size_t)p->nwin * 2 * B * esize;
   cudaError_t e = cudaMalloc((void**)&p->edges, 2 * p->edge_half);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->red, 2 * swept::kReduceBlocks * sizeof(double));
   if (e != cudaSuccess) {
@@ -221,7 +234,7 @@ namespace {
 
 // Enqueue the stage sequence of one advance (Section 3's stages, A5's schedule).
 int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
-  const int64_t levels = p->rk2 ? 2 * nsteps : nsteps;    // sub-timesteps
+  const int64_t levels = p->subs * nsteps;                // sub-timesteps
   const int64_t H = p->H;
   const int64_t q = levels / H;
   const int rem = (int)(levels % H);
@@ -347,7 +360,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
                   int K_cycles, void* stream) {
   if (!p || !u0 || !lam_T || !grad || nsteps < 0) return SWEPT_EINVAL;
   if (!aligned16(u0) || !aligned16(lam_T) || !aligned16(grad)) return SWEPT_EINVAL;
-  if (p->dtype != SWEPT_F64 || p->rk2) return SWEPT_ENOTSUP;
+  if (p->dtype != SWEPT_F64 || p->subs > 1) return SWEPT_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)p->N * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(grad, lam_T, bytes, cudaMemcpyDeviceToDevice, s);
@@ -404,6 +417,25 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
 int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->stencil == SWEPT_EULER) {
+    // per time step: q_mid = q - dt/(2dx) dF(q) into scratch, then
+    // q' = q - dt/dx dF(q_mid) into scratch, swap
+    const int64_t N = p->N;
+    double* qm = reinterpret_cast<double*>(p->edges);
+    double* bufs[2] = {static_cast<double*>(u), qm + 3 * N};
+    const double half = 0.5 * p->c.dtdx;
+    cudaError_t e = cudaSuccess;
+    int cur = 0;
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+      e = swept::launch_naive_euler(bufs[cur], bufs[cur], qm, N, half, p->c.g1, s);
+      if (e == cudaSuccess)
+        e = swept::launch_naive_euler(qm, bufs[cur], bufs[cur ^ 1], N, p->c.dtdx, p->c.g1, s);
+      cur ^= 1;
+    }
+    if (e == cudaSuccess && cur == 1)
+      e = cudaMemcpyAsync(u, bufs[1], (size_t)N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return cuda_status(e);
+  }
   if (p->rk2) {
     // per time step: m = A(u) into scratch, then u' = B(u, m) into scratch, swap
     double* m = reinterpret_cast<double*>(p->edges);

@@ -1,4 +1,4 @@
-// Naive per-step stepper: the "straight" decomposition the swept rule is
+// Naive per-step steppers: the "straight" decomposition the swept rule is
 // measured against (Section 6 compares the two on the same discretisation).
 // One launch per sub-timestep; every launch reads the whole field once and
 // writes it once, so the kernel is bound by HBM bandwidth.
@@ -119,7 +119,67 @@ naive_rk2_kernel(int sub, const double* __restrict__ u, const double* __restrict
   st_chunk<kV>(out + i0, sub == 0 ? t.m : t.u);
 }
 
+// Euler equations, one stage of the midpoint rule per launch (the slopes
+// and the flux update fused: radius 2 in the argument).  A block owns T
+// consecutive points; it stages the argument of points [b0-2, b0+T+2) in
+// shared memory, then the minmod slopes of [b0-1, b0+T+1), then the T+1
+// faces between them, and updates its points:
+//   out_i = fma(-ca, F_{i+1/2} - F_{i-1/2}, base_i).
+// Each face is evaluated once, as in the swept kernels, with the same
+// expressions, so the results agree bit for bit.
+constexpr int kEulerT = 128;
+
+__global__ void __launch_bounds__(kEulerT)
+naive_euler_kernel(const double* __restrict__ arg, const double* __restrict__ base, double* __restrict__ out,
+                   int64_t N, double ca, double g1) {
+  __shared__ double sa[3][kEulerT + 4], ss[3][kEulerT + 2], sf[3][kEulerT + 1];
+  const int64_t b0 = (int64_t)blockIdx.x * kEulerT;
+  for (int j = threadIdx.x; j < kEulerT + 4; j += kEulerT) {
+    int64_t g = (b0 - 2 + j) % N;
+    if (g < 0) g += N;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sa[c][j] = arg[c * N + g];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kEulerT + 2; j += kEulerT) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      ss[c][j] = minmod(__dsub_rn(sa[c][j + 1], sa[c][j]), __dsub_rn(sa[c][j + 2], sa[c][j + 1]));
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < kEulerT + 1; f += kEulerT) {
+    // face between points b0-1+f (left) and b0+f (right)
+    double aL[3], sL[3], aR[3], sR[3], F[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      aL[c] = sa[c][f + 1];
+      sL[c] = ss[c][f];
+      aR[c] = sa[c][f + 2];
+      sR[c] = ss[c][f + 1];
+    }
+    euler_face(aL, sL, aR, sR, g1, F);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sf[c][f] = F[c];
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  const int64_t g = b0 + j;
+  if (g < N) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      out[c * N + g] = __fma_rn(-ca, __dsub_rn(sf[c][j + 1], sf[c][j]), base[c * N + g]);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_naive_euler(const double* arg, const double* base, double* out, int64_t N, double ca,
+                               double g1, cudaStream_t s) {
+  if (N <= 0) return cudaErrorInvalidValue;
+  const int64_t grid = (N + kEulerT - 1) / kEulerT;
+  naive_euler_kernel<<<(unsigned)grid, kEulerT, 0, s>>>(arg, base, out, N, ca, g1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
                              const Consts& c, cudaStream_t s) {

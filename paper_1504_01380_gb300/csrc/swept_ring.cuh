@@ -168,10 +168,11 @@ struct RingImpl {
           if (empty) capture_all<J>(t, s0, s1, mp, P, cl, lane, std::make_integer_sequence<int, 2 * R>{});
           if (fill) place_all<J>(t, al, ar, P, cl, lane, std::make_integer_sequence<int, 2 * R>{});
         });
-        // Runge-Kutta: both windows are at levels of the same parity (h is
-        // even), so one sub-timestep serves the whole ring
+        // Several sub-timesteps per step: both windows are at the same
+        // level modulo Subs (h is a multiple of Subs), so one sub-timestep
+        // serves the whole ring
         tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, nullptr,
-                                     IsRK2<ST>::value ? (int)((a.lev_fill + mp) & 1) : 0);
+                                     (int)((a.lev_fill + mp) & (Subs<ST>::value - 1)));
         if (++j == L) { j = 0; ++P; }
       }
       __syncwarp();

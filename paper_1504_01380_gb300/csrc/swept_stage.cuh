@@ -65,8 +65,8 @@ struct StageImpl {
       int64_t g = ws + (int64_t)lane * K;
       if (g >= a.N) g -= a.N;
       ld_chunk<K>(a.tape + (a.tape_len - tau) * a.N + g, cf.u);
-    } else if constexpr (IsRK2<ST>::value) {
-      cf.sub = (int)((tau - 1) & 1);
+    } else if constexpr (Subs<ST>::value > 1) {
+      cf.sub = (int)((tau - 1) & (Subs<ST>::value - 1));
       (void)a; (void)ws; (void)lane;
     } else {
       (void)cf; (void)a; (void)ws; (void)lane; (void)tau;
@@ -74,9 +74,23 @@ struct StageImpl {
   }
   // The value a neighbour contributes to the stencil: u (or hi); for the
   // Runge-Kutta pair, u in sub-timestep A and m in B.
+  // Euler equations: (q, slopes) for sub-timesteps 0, 1 and (q_mid, slopes) for 2, 3.
   static __device__ __forceinline__ C arg_of(const E& v, int sub) {
-    if constexpr (IsRK2<ST>::value) return sub ? v.y : v.x;
-    else { (void)sub; return Tile<DT, K>::hi_of(v); }
+    if constexpr (ST == kEuler) {
+      EulerNb n;
+      const int o = sub >= 2 ? 3 : 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        n.a[c] = v.v[o + c];
+        n.s[c] = v.v[6 + c];
+      }
+      return n;
+    } else if constexpr (IsRK2<ST>::value) {
+      return sub ? v.y : v.x;
+    } else {
+      (void)sub;
+      return Tile<DT, K>::hi_of(v);
+    }
   }
 
   // Placement for V-fill level mp = P*L + J: left arm at positions
