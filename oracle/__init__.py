@@ -11,7 +11,8 @@ Contents
   steppers, split/merge of the compensated state, the discrete adjoint, the
   two-stage Runge-Kutta steppers and the Euler-equations finite-volume
   scheme (Section 7: second-order reconstruction with minmod, Roe spectral
-  radius dissipation, midpoint rule; four sub-timesteps per time step).
+  radius dissipation, midpoint rule; four sub-timesteps per time step), in
+  FP64 and on the compensated FP32 state (binary32 fluxes, TwoSum update).
   These follow the definition the swept rule reorders (Sections 2-3): one
   sub-timestep applied to every point of the periodic grid, level after level.
 * ``pointwise.py``: the same sub-timestep for a single point in Python, with
@@ -79,10 +80,12 @@ def lib():
             L.oracle_advance_rk2_f64.argtypes = [i32, dp, dp, i64, i64, i32]
             L.oracle_rk2_substep_f64.argtypes = [i32, dp, i32, dp, dp, dp, i64]
             L.oracle_euler_advance.argtypes = [dp, dp, i64, i64]
+            L.oracle_euler_advance_f32c.argtypes = [dp, fp, fp, i64, i64]
             for f in ("oracle_step_f64", "oracle_advance_f64", "oracle_split_f32c",
                       "oracle_merge_f32c", "oracle_step_f32c", "oracle_advance_f32c",
                       "oracle_adjoint_f64", "oracle_adjoint_step_f64", "oracle_max_threads",
-                      "oracle_advance_rk2_f64", "oracle_rk2_substep_f64", "oracle_euler_advance"):
+                      "oracle_advance_rk2_f64", "oracle_rk2_substep_f64", "oracle_euler_advance",
+                      "oracle_euler_advance_f32c"):
                 getattr(L, f).restype = i32
             _lib = L
         return _lib
@@ -218,6 +221,20 @@ def euler_advance(params, q: np.ndarray, nsteps: int) -> np.ndarray:
         raise ValueError("Euler takes (dt, dx, gamma)")
     _check(lib().oracle_euler_advance(_ptr(p), _ptr(q), q.shape[0], int(nsteps)), "euler_advance")
     return q
+
+
+def euler_advance_f32c(params, hi: np.ndarray, lo: np.ndarray, nsteps: int):
+    """Euler equations on the compensated state (hi, lo), each of shape (N, 3) float32."""
+    hi = np.array(hi, dtype=np.float32, copy=True, order="C")
+    lo = np.array(lo, dtype=np.float32, copy=True, order="C")
+    if hi.ndim != 2 or hi.shape[1] != 3 or lo.shape != hi.shape:
+        raise ValueError("hi and lo must have shape (N, 3)")
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    if p.size != 3:
+        raise ValueError("Euler takes (dt, dx, gamma)")
+    _check(lib().oracle_euler_advance_f32c(_ptr(p), _ptr(hi), _ptr(lo), hi.shape[0], int(nsteps)),
+           "euler_advance_f32c")
+    return hi, lo
 
 
 def max_threads() -> int:

@@ -438,6 +438,95 @@ int oracle_euler_advance(const double *prm, double *q, int64_t n, int64_t nsteps
     return OR_OK;
 }
 
+/*
+ * Euler equations with the FP32-compensated state (the precision of the
+ * compensated heat and KS steppers above): q = hi + lo per component, fluxes
+ * and slopes in FP32 from hi (or from the FP32 midpoint), the update added
+ * to lo and renormalised by TwoSum.  Same expressions as the FP64 scheme
+ * above with every operation in binary32 (/ and sqrtf correctly rounded):
+ *   slopes of the argument a (hi, then q_mid): s = minmodf(a_i - a_{i-1}, a_{i+1} - a_i)
+ *   midpoint:  y = fmaf(-ch, F_{i+1/2} - F_{i-1/2}, lo_i);  q_mid_i = hi_i + y
+ *   full step: y = fmaf(-cf, F_{i+1/2} - F_{i-1/2}, lo_i);  (hi_i, lo_i) = TwoSum(hi_i, y)
+ * with fluxes from (hi, s) for the midpoint and from (q_mid, s) for the full
+ * step; cf = (float)(dt/dx), ch = 0.5f * cf, g1 = (float)(gamma - 1).
+ */
+static inline float minmodf_(float a, float b)
+{
+    if (a > 0.0f && b > 0.0f) return fminf(a, b);
+    if (a < 0.0f && b < 0.0f) return fmaxf(a, b);
+    return 0.0f;
+}
+
+static void euler_face_flux_f(const float *qL, const float *qR, float g1, float *F)
+{
+    float uL = qL[1] / qL[0], uR = qR[1] / qR[0];
+    float pL = g1 * (qL[2] - 0.5f * (qL[1] * uL));
+    float pR = g1 * (qR[2] - 0.5f * (qR[1] * uR));
+    float eL = qL[2] + pL, eR = qR[2] + pR;
+    float HL = eL / qL[0], HR = eR / qR[0];
+    float fL[3] = {qL[1], fmaf(qL[1], uL, pL), eL * uL};
+    float fR[3] = {qR[1], fmaf(qR[1], uR, pR), eR * uR};
+    float sl = sqrtf(qL[0]), sr = sqrtf(qR[0]);
+    float d = sl + sr;
+    float ut = (sl * uL + sr * uR) / d;
+    float Ht = (sl * HL + sr * HR) / d;
+    float c2 = g1 * (Ht - 0.5f * (ut * ut));
+    float lam = fabsf(ut) + sqrtf(fmaxf(c2, 0.0f));
+    for (int k = 0; k < 3; ++k) F[k] = 0.5f * ((fL[k] + fR[k]) - lam * (qR[k] - qL[k]));
+}
+
+static void euler_slopes_f(const float *a, float *s, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t im = wrap(i - 1, n), ip = wrap(i + 1, n);
+        for (int k = 0; k < 3; ++k)
+            s[3 * i + k] = minmodf_(a[3 * i + k] - a[3 * im + k], a[3 * ip + k] - a[3 * i + k]);
+    }
+}
+
+/* dF[3i+k] = F_{i+1/2,k} - F_{i-1/2,k} with fluxes from (a, s). */
+static void euler_flux_diff_f(const float *a, const float *s, float g1, float *dF, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float Fl[3], Fr[3], qL[3], qR[3];
+        int64_t im = wrap(i - 1, n), ip = wrap(i + 1, n);
+        for (int k = 0; k < 3; ++k) {
+            qL[k] = fmaf(0.5f, s[3 * im + k], a[3 * im + k]);
+            qR[k] = fmaf(-0.5f, s[3 * i + k], a[3 * i + k]);
+        }
+        euler_face_flux_f(qL, qR, g1, Fl);
+        for (int k = 0; k < 3; ++k) {
+            qL[k] = fmaf(0.5f, s[3 * i + k], a[3 * i + k]);
+            qR[k] = fmaf(-0.5f, s[3 * ip + k], a[3 * ip + k]);
+        }
+        euler_face_flux_f(qL, qR, g1, Fr);
+        for (int k = 0; k < 3; ++k) dF[3 * i + k] = Fr[k] - Fl[k];
+    }
+}
+
+/* (hi, lo): 3n floats each, point-major; nsteps time steps of 4 sub-timesteps. */
+int oracle_euler_advance_f32c(const double *prm, float *hi, float *lo, int64_t n, int64_t nsteps)
+{
+    if (n <= 0 || nsteps < 0 || !(prm[1] > 0.0)) return OR_EINVAL;
+    const float cf = (float)(prm[0] / prm[1]);
+    const float ch = 0.5f * cf;
+    const float g1 = (float)(prm[2] - 1.0);
+    float *s = (float *)malloc((size_t)3 * n * sizeof(float));
+    float *qm = (float *)malloc((size_t)3 * n * sizeof(float));
+    float *dF = (float *)malloc((size_t)3 * n * sizeof(float));
+    if (!s || !qm || !dF) { free(s); free(qm); free(dF); return OR_ENOMEM; }
+    for (int64_t t = 0; t < nsteps; ++t) {
+        euler_slopes_f(hi, s, n);
+        euler_flux_diff_f(hi, s, g1, dF, n);
+        for (int64_t j = 0; j < 3 * n; ++j) qm[j] = hi[j] + fmaf(-ch, dF[j], lo[j]);
+        euler_slopes_f(qm, s, n);
+        euler_flux_diff_f(qm, s, g1, dF, n);
+        for (int64_t j = 0; j < 3 * n; ++j) two_sum(hi[j], fmaf(-cf, dF[j], lo[j]), &hi[j], &lo[j]);
+    }
+    free(s); free(qm); free(dF);
+    return OR_OK;
+}
+
 /* ------------------------------------------------------- adjoint ------ */
 
 /*

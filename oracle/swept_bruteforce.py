@@ -32,6 +32,8 @@ general).
 """
 from __future__ import annotations
 
+import numpy as np
+
 from dataclasses import dataclass, field
 
 from .pointwise import make_point_update
@@ -65,11 +67,16 @@ def swept_simulate(stencil: int, params, u0, P: int, nsteps: int, max_stages: in
     store = [dict() for _ in range(P)]
     pair = stencil in (2, 3)            # two-stage Runge-Kutta: (u, m) per point
     euler = stencil == 4                # Euler: (q, q_mid, slopes), q = u0[x] (3 values)
+    euler32 = stencil == 5              # compensated FP32 Euler: u0[x] = (hi(3), lo(3)) float32
     for j in range(P):
         for x in range(j * B, (j + 1) * B):
             if euler:
                 q = tuple(float(c) for c in u0[x])
                 v = q + q + (0.0, 0.0, 0.0)
+            elif euler32:
+                h = tuple(np.float32(c) for c in u0[x][:3])
+                lo = tuple(np.float32(c) for c in u0[x][3:6])
+                v = h + lo + h + (np.float32(0.0),) * 3
             else:
                 v0 = float(u0[x])
                 v = (v0, v0) if pair else v0
@@ -147,6 +154,6 @@ def swept_simulate(stencil: int, params, u0, P: int, nsteps: int, max_stages: in
     for j in range(P):
         for (x, t), (v, _) in store[j].items():
             if t == nsteps and final[x] is None:
-                final[x] = v[0] if pair else (v[:3] if euler else v)
+                final[x] = v[0] if pair else (v[:3] if euler else (v[:6] if euler32 else v))
     trace.u_final = final
     return trace

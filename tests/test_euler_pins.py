@@ -153,3 +153,84 @@ def test_euler_swept_bruteforce_matches_per_step(B, nsteps):
     got = np.array(tr.u_final)
     assert np.array_equal(got, oracle.euler_advance(prm, q, nsteps))
     assert all(c == 1 for c in tr.compute_count.values())
+
+
+# ----------------------------------------------------------------------------
+# Compensated FP32 state (hi, lo): fluxes in binary32, update compensated
+# ----------------------------------------------------------------------------
+
+def split3(q):
+    hi, lo = oracle.split_f32c(np.ascontiguousarray(q).reshape(-1))
+    return hi.reshape(-1, 3), lo.reshape(-1, 3)
+
+
+def merge3(hi, lo):
+    return oracle.merge_f32c(hi.reshape(-1), lo.reshape(-1)).reshape(-1, 3)
+
+
+def perturbed_sod(n):
+    x, q = sod_periodic(n)
+    q[:, 1] = 0.3 * np.sin(2 * np.pi * x)
+    q[:, 2] += 0.5 * q[:, 1] ** 2 / q[:, 0]
+    return x, q
+
+
+@pytest.mark.parametrize("B", [4, 8])
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_f32c_binary32_restatement_and_swept_match(B, nsteps):
+    """An independent binary32 restatement (numpy float32 operations, exact-rational fma
+    rounded once), run through the swept stages, equals the C oracle bit for bit."""
+    n = 16
+    x, q = perturbed_sod(n)
+    prm = [0.2 / n, 1.0 / n, GAMMA]
+    hi, lo = split3(q)
+    tr = swept_simulate(5, prm, np.concatenate([hi, lo], axis=1), n // B, 4 * nsteps)
+    got = np.array([[float(c) for c in v] for v in tr.u_final])
+    h2, l2 = oracle.euler_advance_f32c(prm, hi, lo, nsteps)
+    assert np.array_equal(got[:, :3], h2) and np.array_equal(got[:, 3:], l2)
+    assert all(c == 1 for c in tr.compute_count.values())
+
+
+def test_f32c_uniform_state_is_fixed_exactly():
+    hi, lo = split3(np.tile([0.7, 0.35, 2.5], (40, 1)))
+    h2, l2 = oracle.euler_advance_f32c([0.001, 0.02, GAMMA], hi, lo, 50)
+    assert np.array_equal(h2, hi) and np.array_equal(l2, lo)
+
+
+@pytest.mark.parametrize("n,steps", [(128, 60), (256, 200)])
+def test_f32c_tracks_the_fp64_scheme(n, steps):
+    """Binary32 fluxes carry relative rounding ~6e-8 per operation; limiter switches at the
+    discontinuities amplify it locally.  Measured up to 3.5e-5; a dropped or misplaced term
+    differs at O(1e-2) or more."""
+    x, q = perturbed_sod(n)
+    prm = [0.2 / n, 1.0 / n, GAMMA]
+    a = oracle.euler_advance(prm, q, steps)
+    b = merge3(*oracle.euler_advance_f32c(prm, *split3(q), steps))
+    assert np.max(np.abs(a - b) / (np.abs(a) + 1.0)) <= 2e-4
+
+
+def test_f32c_conservation():
+    """The flux differences telescope; only the rounding of each increment remains, which the
+    compensated (hi, lo) update keeps at the 1e-9 relative level (measured 1.6e-9)."""
+    n = 256
+    x, q = perturbed_sod(n)
+    hi, lo = oracle.euler_advance_f32c([0.2 / n, 1.0 / n, GAMMA], *split3(q), 200)
+    out = merge3(hi, lo)
+    for k in range(3):
+        scale = math.fsum(np.abs(q[:, k]))
+        assert abs(math.fsum(out[:, k]) - math.fsum(q[:, k])) <= 1e-8 * scale
+
+
+def test_f32c_sod_against_exact_riemann_and_converges():
+    t = 0.1
+    errs = []
+    for n in (200, 800):
+        x, q = sod_periodic(n)
+        dt = 0.2 / n
+        steps = int(round(t / dt))
+        out = merge3(*oracle.euler_advance_f32c([dt, 1.0 / n, GAMMA], *split3(q), steps))
+        rho, u, p = prim(out)
+        assert np.all(rho > 0) and np.all(p > 0)
+        errs.append(np.mean(np.abs(rho - sod_exact_density(x, steps * dt))))
+    assert errs[0] < 0.02
+    assert errs[1] < 0.6 * errs[0]
