@@ -23,8 +23,10 @@
  *   SWEPT_F64  : double u[N].
  *   SWEPT_F32C : float hi[N] followed by float lo[N] (8N bytes); the value
  *                of point i is hi[i] + lo[i] (compensated FP32).
- *   SWEPT_EULER plans (FP64): double rho[N], then m[N], then E[N] (24N
- *                bytes; the conserved variables density, momentum, energy).
+ *   SWEPT_EULER plans: the conserved variables density, momentum, energy.
+ *                FP64: double rho[N], m[N], E[N] (24N bytes).  F32C: float
+ *                hi of rho, m, E (3N), then lo of rho, m, E (3N) (24N bytes):
+ *                the F32C layout of the 3N values rho, m, E.
  */
 #ifndef SWEPT_H
 #define SWEPT_H
@@ -64,8 +66,12 @@ extern "C" {
  * One time step is four sub-timesteps (Section 2): slopes of q, half-step
  * flux update into q_mid, slopes of q_mid, full-step flux update of q with
  * q_mid's fluxes.  nsteps counts time steps.  params = {dt, dx, gamma}
- * (nparams = 3, dx > 0, dt >= 0, gamma > 1).  B in {32, 64, 128}; 9-value
- * point states (72 bytes) exist on chip and in the edge buffers. */
+ * (nparams = 3, dx > 0, dt >= 0, gamma > 1).  FP64: B in {32, 64, 128},
+ * 9-value point states (72 bytes) on chip and in the edge buffers.  F32C:
+ * fluxes and slopes in binary32 from hi (and from a binary32 midpoint), the
+ * full-step increment added to lo and renormalised by TwoSum, as in the
+ * compensated heat and KS updates; B in {32, 64, 128, 256}, 12-float point
+ * states (48 bytes). */
 #define SWEPT_EULER     4
 
 /* Status codes. */
@@ -101,7 +107,8 @@ typedef struct swept_plan_s *swept_plan_t;
  *           general B % (2*radius) == 0).  B = 0 picks the tuned default.
  *   params  host pointer; copied.
  * Allocates the edge double-buffer (2 * 2N values, 32N bytes; 64N for the
- * Runge-Kutta pairs; 288N for Euler point states) on the current device.
+ * Runge-Kutta pairs; 288N / 192N for FP64 / F32C Euler point states) on
+ * the current device.
  * *out is set on success.
  * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP, SWEPT_ENOMEM, SWEPT_ECUDA.
  */
@@ -118,7 +125,10 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  * swept_plan_set -- tuning options of a plan (used by the autotuner and the
  * tests; results do not depend on them, only speed does).
  *   SWEPT_OPT_DIAMOND    kernel for full diamond stages:
- *                        SWEPT_DIAMOND_AUTO (default), SWEPT_DIAMOND_WINDOW
+ *                        SWEPT_DIAMOND_AUTO (default: the ring from 8
+ *                        windows up, except that with automatic ring warps
+ *                        the per-window kernel runs when the GPU holds a
+ *                        warp for every window at once), SWEPT_DIAMOND_WINDOW
  *                        (one warp per window), SWEPT_DIAMOND_RING (one warp
  *                        streams a run of windows, overlapping the V-fill of
  *                        one with the triangle of the previous).

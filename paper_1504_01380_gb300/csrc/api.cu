@@ -53,6 +53,8 @@ int make_consts(int stencil, const double* p, int np, Consts& c) {
     if (np < 3 || !(p[1] > 0.0) || !(p[0] >= 0.0) || !(p[2] > 1.0)) return SWEPT_EINVAL;
     c.dtdx = p[0] / p[1];
     c.g1 = p[2] - 1.0;
+    c.dtdx32 = (float)c.dtdx;
+    c.g132 = (float)c.g1;
     return SWEPT_OK;
   }
   if (stencil == SWEPT_HEAT_RK2 || stencil == SWEPT_KS_RK2) stencil -= 2;   // same constants
@@ -80,7 +82,9 @@ int make_consts(int stencil, const double* p, int np, Consts& c) {
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
-  if (p->stencil == SWEPT_EULER) return swept::launch_stage_euler_f64(p->K, a, s);
+  if (p->stencil == SWEPT_EULER)
+    return p->dtype == SWEPT_F64 ? swept::launch_stage_euler_f64(p->K, a, s)
+                                 : swept::launch_stage_euler_f32c(p->K, a, s);
   if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_stage_heatrk2_f64(p->K, a, s);
   if (p->stencil == SWEPT_KS_RK2) return swept::launch_stage_ksrk2_f64(p->K, a, s);
   if (p->stencil == SWEPT_HEAT)
@@ -90,15 +94,21 @@ cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t
                                : swept::launch_stage_ks_f32c(p->K, a, s);
 }
 
+// Full diamond stage on the ring kernel.  Under SWEPT_DIAMOND_AUTO with
+// automatic warps the launcher may pick the per-window kernel instead (when
+// every window gets a resident warp at once).
 cudaError_t launch_ring(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
-  if (p->stencil == SWEPT_EULER) return swept::launch_ring_euler_f64(p->K, a, p->ring_warps, s);
-  if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_ring_heatrk2_f64(p->K, a, p->ring_warps, s);
-  if (p->stencil == SWEPT_KS_RK2) return swept::launch_ring_ksrk2_f64(p->K, a, p->ring_warps, s);
+  const int w = (p->diamond == SWEPT_DIAMOND_AUTO && p->ring_warps == 0) ? -1 : p->ring_warps;
+  if (p->stencil == SWEPT_EULER)
+    return p->dtype == SWEPT_F64 ? swept::launch_ring_euler_f64(p->K, a, w, s)
+                                 : swept::launch_ring_euler_f32c(p->K, a, w, s);
+  if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_ring_heatrk2_f64(p->K, a, w, s);
+  if (p->stencil == SWEPT_KS_RK2) return swept::launch_ring_ksrk2_f64(p->K, a, w, s);
   if (p->stencil == SWEPT_HEAT)
-    return p->dtype == SWEPT_F64 ? swept::launch_ring_heat_f64(p->K, a, p->ring_warps, s)
-                                 : swept::launch_ring_heat_f32c(p->K, a, p->ring_warps, s);
-  return p->dtype == SWEPT_F64 ? swept::launch_ring_ks_f64(p->K, a, p->ring_warps, s)
-                               : swept::launch_ring_ks_f32c(p->K, a, p->ring_warps, s);
+    return p->dtype == SWEPT_F64 ? swept::launch_ring_heat_f64(p->K, a, w, s)
+                                 : swept::launch_ring_heat_f32c(p->K, a, w, s);
+  return p->dtype == SWEPT_F64 ? swept::launch_ring_ks_f64(p->K, a, w, s)
+                               : swept::launch_ring_ks_f32c(p->K, a, w, s);
 }
 
 // The ring kernel needs at least two windows per warp to gain over the
@@ -109,10 +119,11 @@ bool use_ring(const swept_plan_s* p) {
   return p->nwin >= 8;
 }
 
-// Default tile width: the largest of 512, 256, ... (64, 32 for the Euler
-// equations) that divides N and keeps K a multiple of the radius.
-int default_B(int64_t N, int radius, int stencil) {
-  for (int K = stencil == SWEPT_EULER ? 2 : 16; K >= 1; K /= 2) {
+// Default tile width: the largest of 512, 256, ... that divides N and keeps
+// K a multiple of the radius (Euler equations: from 64 in FP64, 128 in F32C).
+int default_B(int64_t N, int radius, int stencil, int dtype) {
+  const int kmax = stencil != SWEPT_EULER ? 16 : (dtype == SWEPT_F64 ? 2 : 4);
+  for (int K = kmax; K >= 1; K /= 2) {
     const int B = 32 * K;
     if (K % radius == 0 && N % B == 0) return B;
   }
@@ -148,13 +159,13 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   if (radius != rad) return SWEPT_EINVAL;
   if (dtype != SWEPT_F64 && dtype != SWEPT_F32C) return SWEPT_EINVAL;
   const bool rk2 = stencil_id == SWEPT_HEAT_RK2 || stencil_id == SWEPT_KS_RK2;
-  if ((rk2 || euler) && dtype != SWEPT_F64) return SWEPT_ENOTSUP;
+  if (rk2 && dtype != SWEPT_F64) return SWEPT_ENOTSUP;
   if (N <= 0) return SWEPT_EINVAL;
-  if (B == 0) B = default_B(N, rad, stencil_id);
+  if (B == 0) B = default_B(N, rad, stencil_id, dtype);
   if (B <= 0 || B % 32) return SWEPT_EINVAL;
   const int K = B / 32;
   if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32) return SWEPT_ENOTSUP;
-  if (euler && K > 4) return SWEPT_ENOTSUP;
+  if (euler && K > (dtype == SWEPT_F64 ? 4 : 8)) return SWEPT_ENOTSUP;
   if (K % rad) return SWEPT_EINVAL;
   if (N % B) return SWEPT_EINVAL;
   if (N / B > (int64_t)0x7fffffff) return SWEPT_EINVAL;
@@ -177,7 +188,8 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->rk2 = rk2 ? 1 : 0;
   p->subs = euler ? 4 : (rk2 ? 2 : 1);
   cudaGetDevice(&p->device);
-  const size_t esize = euler ? sizeof(swept::EulerE) : (rk2 ? 16 : 8);
+  const size_t esize = euler ? (dtype == SWEPT_F64 ? sizeof(swept::EulerE) : sizeof(swept::EulerEF))
+                              : (rk2 ? 16 : 8);
   p->edge_half = (size_t)p->nwin * 2 * B * esize;
   cudaError_t e = cudaMalloc((void**)&p->edges, 2 * p->edge_half);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->red, 2 * swept::kReduceBlocks * sizeof(double));
@@ -417,6 +429,27 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
 int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->stencil == SWEPT_EULER && p->dtype == SWEPT_F32C) {
+    // per time step: q_mid = hi + (lo - dt/(2dx) dF(hi)) into scratch, then
+    // (hi', lo') = TwoSum(hi, lo - dt/dx dF(q_mid)) into scratch, swap
+    const int64_t N = p->N;
+    float* qm = reinterpret_cast<float*>(p->edges);
+    float* bufs[2] = {static_cast<float*>(u), qm + 3 * N};
+    const float cf = p->c.dtdx32, ch = 0.5f * p->c.dtdx32, g1 = p->c.g132;
+    cudaError_t e = cudaSuccess;
+    int cur = 0;
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+      const float* hi = bufs[cur];
+      const float* lo = bufs[cur] + 3 * N;
+      e = swept::launch_naive_euler_f32c(0, hi, hi, lo, qm, nullptr, N, ch, g1, s);
+      if (e == cudaSuccess)
+        e = swept::launch_naive_euler_f32c(1, qm, hi, lo, bufs[cur ^ 1], bufs[cur ^ 1] + 3 * N, N, cf, g1, s);
+      cur ^= 1;
+    }
+    if (e == cudaSuccess && cur == 1)
+      e = cudaMemcpyAsync(u, bufs[1], (size_t)N * 6 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return cuda_status(e);
+  }
   if (p->stencil == SWEPT_EULER) {
     // per time step: q_mid = q - dt/(2dx) dF(q) into scratch, then
     // q' = q - dt/dx dF(q_mid) into scratch, swap

@@ -120,36 +120,42 @@ naive_rk2_kernel(int sub, const double* __restrict__ u, const double* __restrict
 }
 
 // Euler equations, one stage of the midpoint rule per launch (the slopes
-// and the flux update fused: radius 2 in the argument).  A block owns T
-// consecutive points; it stages the argument of points [b0-2, b0+T+2) in
-// shared memory, then the minmod slopes of [b0-1, b0+T+1), then the T+1
-// faces between them, and updates its points:
-//   out_i = fma(-ca, F_{i+1/2} - F_{i-1/2}, base_i).
-// Each face is evaluated once, as in the swept kernels, with the same
-// expressions, so the results agree bit for bit.
+// and the flux update fused: radius 2 in the argument).  A block of T
+// threads evaluates T consecutive faces, one per thread, and updates the
+// T - 1 points between them; it first stages the argument of points
+// [b0-2, b0+T+1) in shared memory, then the minmod slopes of [b0-1, b0+T).
+// Updates (dF = F_{i+1/2} - F_{i-1/2}):
+//   MODE 0 (FP64):              out = fma(-ca, dF, base)
+//   MODE 1 (F32C, midpoint):    out = hi + fma(-ca, dF, lo)
+//   MODE 2 (F32C, full step):   (out, out_lo) = TwoSum(hi, fma(-ca, dF, lo))
+// with base / hi = `base` and lo = `lo`.  Each face is evaluated once, with
+// the expressions of the swept kernels, so the results agree bit for bit.
 constexpr int kEulerT = 128;
 
+template <class T, int MODE>
 __global__ void __launch_bounds__(kEulerT)
-naive_euler_kernel(const double* __restrict__ arg, const double* __restrict__ base, double* __restrict__ out,
-                   int64_t N, double ca, double g1) {
-  __shared__ double sa[3][kEulerT + 4], ss[3][kEulerT + 2], sf[3][kEulerT + 1];
-  const int64_t b0 = (int64_t)blockIdx.x * kEulerT;
-  for (int j = threadIdx.x; j < kEulerT + 4; j += kEulerT) {
+naive_euler_kernel(const T* __restrict__ arg, const T* __restrict__ base, const T* __restrict__ lo,
+                   T* __restrict__ out, T* __restrict__ out_lo, int64_t N, T ca, T g1) {
+  using O = EOps<T>;
+  __shared__ T sa[3][kEulerT + 3], ss[3][kEulerT + 1], sf[3][kEulerT];
+  const int64_t b0 = (int64_t)blockIdx.x * (kEulerT - 1);
+  for (int j = threadIdx.x; j < kEulerT + 3; j += kEulerT) {
     int64_t g = (b0 - 2 + j) % N;
     if (g < 0) g += N;
 #pragma unroll
     for (int c = 0; c < 3; ++c) sa[c][j] = arg[c * N + g];
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < kEulerT + 2; j += kEulerT) {
+  for (int j = threadIdx.x; j < kEulerT + 1; j += kEulerT) {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      ss[c][j] = minmod(__dsub_rn(sa[c][j + 1], sa[c][j]), __dsub_rn(sa[c][j + 2], sa[c][j + 1]));
+      ss[c][j] = minmod<T>(O::sub(sa[c][j + 1], sa[c][j]), O::sub(sa[c][j + 2], sa[c][j + 1]));
   }
   __syncthreads();
-  for (int f = threadIdx.x; f < kEulerT + 1; f += kEulerT) {
-    // face between points b0-1+f (left) and b0+f (right)
-    double aL[3], sL[3], aR[3], sR[3], F[3];
+  {
+    // face f between points b0-1+f (left) and b0+f (right)
+    const int f = threadIdx.x;
+    T aL[3], sL[3], aR[3], sR[3], F[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       aL[c] = sa[c][f + 1];
@@ -157,17 +163,29 @@ naive_euler_kernel(const double* __restrict__ arg, const double* __restrict__ ba
       aR[c] = sa[c][f + 2];
       sR[c] = ss[c][f + 1];
     }
-    euler_face(aL, sL, aR, sR, g1, F);
+    euler_face<T>(aL, sL, aR, sR, g1, F);
 #pragma unroll
     for (int c = 0; c < 3; ++c) sf[c][f] = F[c];
   }
   __syncthreads();
   const int j = threadIdx.x;
   const int64_t g = b0 + j;
-  if (g < N) {
+  if (j < kEulerT - 1 && g < N) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      out[c * N + g] = __fma_rn(-ca, __dsub_rn(sf[c][j + 1], sf[c][j]), base[c * N + g]);
+    for (int c = 0; c < 3; ++c) {
+      const T dF = O::sub(sf[c][j + 1], sf[c][j]);
+      const int64_t x = c * N + g;
+      if constexpr (MODE == 0) {
+        out[x] = O::fma(-ca, dF, base[x]);
+      } else if constexpr (MODE == 1) {
+        out[x] = O::add(base[x], O::fma(-ca, dF, lo[x]));
+      } else {
+        float h, l;
+        two_sum(base[x], O::fma(-ca, dF, lo[x]), h, l);
+        out[x] = h;
+        out_lo[x] = l;
+      }
+    }
   }
 }
 
@@ -176,8 +194,19 @@ naive_euler_kernel(const double* __restrict__ arg, const double* __restrict__ ba
 cudaError_t launch_naive_euler(const double* arg, const double* base, double* out, int64_t N, double ca,
                                double g1, cudaStream_t s) {
   if (N <= 0) return cudaErrorInvalidValue;
-  const int64_t grid = (N + kEulerT - 1) / kEulerT;
-  naive_euler_kernel<<<(unsigned)grid, kEulerT, 0, s>>>(arg, base, out, N, ca, g1);
+  const int64_t grid = (N + kEulerT - 2) / (kEulerT - 1);
+  naive_euler_kernel<double, 0><<<(unsigned)grid, kEulerT, 0, s>>>(arg, base, nullptr, out, nullptr, N, ca, g1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_naive_euler_f32c(int full, const float* arg, const float* hi, const float* lo, float* out,
+                                    float* out_lo, int64_t N, float ca, float g1, cudaStream_t s) {
+  if (N <= 0) return cudaErrorInvalidValue;
+  const int64_t grid = (N + kEulerT - 2) / (kEulerT - 1);
+  if (full)
+    naive_euler_kernel<float, 2><<<(unsigned)grid, kEulerT, 0, s>>>(arg, hi, lo, out, out_lo, N, ca, g1);
+  else
+    naive_euler_kernel<float, 1><<<(unsigned)grid, kEulerT, 0, s>>>(arg, hi, lo, out, nullptr, N, ca, g1);
   return cudaGetLastError();
 }
 

@@ -51,20 +51,29 @@ cudaError_t launch_stage_heatrk2_f64(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_ksrk2_f64(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_ring_heatrk2_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 cudaError_t launch_ring_ksrk2_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
-// Euler equations (FP64, planar rho/m/E state, 72-byte edge elements); K in {1, 2, 4}.
+// Euler equations: FP64 (planar rho/m/E state, 72-byte edge elements, K in
+// {1, 2, 4}) and compensated FP32 (hi[3N], lo[3N]; 48-byte edge elements,
+// K in {1, 2, 4, 8}).
 cudaError_t launch_stage_euler_f64(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_ring_euler_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+cudaError_t launch_stage_euler_f32c(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_ring_euler_f32c(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 // Naive Euler stage of the midpoint rule on the planar state: out = base -
 // ca (F_{i+1/2} - F_{i-1/2}) with the fluxes of (arg, minmod slopes of arg).
 cudaError_t launch_naive_euler(const double* arg, const double* base, double* out, int64_t N, double ca,
                                double g1, cudaStream_t s);
+// Compensated FP32 version: full = 0: out = hi + fma(-ca, dF, lo) (the
+// midpoint, from arg = hi); full = 1: (out, out_lo) = TwoSum(hi, fma(-ca, dF, lo))
+// (from arg = the midpoint).  All arrays 3N floats, planar.
+cudaError_t launch_naive_euler_f32c(int full, const float* arg, const float* hi, const float* lo, float* out,
+                                    float* out_lo, int64_t N, float ca, float g1, cudaStream_t s);
 // Naive Runge-Kutta sub-timestep: sub 0: m = A(u); sub 1: out = B(u, m).
 cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
                              const Consts& c, cudaStream_t s);
 
 // Shared-memory bytes per block of the stage kernel for tile width B and
-// edge elements of esize bytes (8; 16 for the Runge-Kutta pair; 72 for an
-// Euler point state).
+// edge elements of esize bytes (8; 16 for the Runge-Kutta pair; 72 or 48
+// for an Euler point state).
 inline size_t stage_smem_bytes(int B, int esize = 8) { return (size_t)kWarpsPerBlock * 2 * B * esize; }
 
 // Naive per-step stepper: out = S(in).

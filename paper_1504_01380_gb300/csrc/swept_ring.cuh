@@ -40,6 +40,7 @@
 #include <type_traits>
 
 #include "swept_internal.h"
+#include "swept_stage.cuh"
 
 namespace swept {
 
@@ -210,6 +211,10 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
 
 // Launch with `nwarps` warps; 0 picks min(resident warp slots of the GPU,
 // nwin / 2), so that every warp streams at least two windows when it can.
+// nwarps < 0 is the automatic choice of kernel: when the GPU holds a warp for
+// every window at once, the per-window kernel (2h levels per warp) finishes
+// the stage sooner than ring runs of n windows (n + 1 slots of h levels), so
+// that kernel is launched instead; otherwise as for 0.
 template <int ST, class DT, int K>
 cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
   const size_t smem = ring_smem_bytes<ST, DT, K>();
@@ -223,7 +228,9 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, swept_ring_kernel<ST, DT, K>,
                                                       kWarpsPerBlock * 32, smem);
     if (e != cudaSuccess) return e;
-    nwarps = sms * (per_sm > 0 ? per_sm : 1) * kWarpsPerBlock;
+    const int resident = sms * (per_sm > 0 ? per_sm : 1) * kWarpsPerBlock;
+    if (nwarps < 0 && a.nwin <= resident) return launch_stage_k<ST, DT, K>(a, s);
+    nwarps = resident;
     if (nwarps > a.nwin / 2) nwarps = a.nwin / 2;
     if (nwarps < 1) nwarps = 1;
   }

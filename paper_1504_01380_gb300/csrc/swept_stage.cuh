@@ -74,17 +74,10 @@ struct StageImpl {
   }
   // The value a neighbour contributes to the stencil: u (or hi); for the
   // Runge-Kutta pair, u in sub-timestep A and m in B.
-  // Euler equations: (q, slopes) for sub-timesteps 0, 1 and (q_mid, slopes) for 2, 3.
+  // Euler equations: (q or hi, slopes) for sub-timesteps 0, 1 and (q_mid, slopes) for 2, 3.
   static __device__ __forceinline__ C arg_of(const E& v, int sub) {
     if constexpr (ST == kEuler) {
-      EulerNb n;
-      const int o = sub >= 2 ? 3 : 0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        n.a[c] = v.v[o + c];
-        n.s[c] = v.v[6 + c];
-      }
-      return n;
+      return EulerSide<DT>::nb(v, sub);
     } else if constexpr (IsRK2<ST>::value) {
       return sub ? v.y : v.x;
     } else {

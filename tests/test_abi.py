@@ -65,8 +65,8 @@ def _plan_rc(lib, N, radius, stencil, params, dtype, B):
     (0, 1, 0, [0.25], 0, 32, -1),           # empty grid
     (1024, 2, 1, [0.002, 0.0], 0, 64, -1),  # dx must be positive
     (1024, 2, 1, [0.002], 0, 64, -1),       # KS needs two parameters
-    (1024, 1, 4, [1e-4, 1e-3, 1.4], 1, 32, -5),   # Euler equations: FP64 only
-    (1024, 1, 4, [1e-4, 1e-3, 1.4], 0, 256, -5),  # Euler equations: B <= 128
+    (1024, 1, 4, [1e-4, 1e-3, 1.4], 1, 512, -5),  # compensated Euler: B <= 256
+    (1024, 1, 4, [1e-4, 1e-3, 1.4], 0, 256, -5),  # FP64 Euler: B <= 128
     (1024, 2, 4, [1e-4, 1e-3, 1.4], 0, 32, -1),   # Euler radius is 1
     (1024, 1, 4, [1e-4, 1e-3], 0, 32, -1),        # Euler needs {dt, dx, gamma}
     (1024, 1, 4, [1e-4, 1e-3, 1.0], 0, 32, -1),   # gamma must exceed 1
