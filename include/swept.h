@@ -300,6 +300,18 @@ int swept_batch_info(swept_batch_t batch, int64_t *info, int ninfo);
  */
 int swept_advance_batch(swept_batch_t batch, void *pool, void *stream);
 
+/*
+ * swept_batch_naive_advance -- the same result by per-step stepping over the
+ * whole batch: one launch per time step covering every problem that still
+ * has steps left (Section 6's straight decomposition, batched: one read and
+ * one write of every active state per step).  The baseline the persistent
+ * swept launch is measured against.  Allocates a scratch pool (the extent of
+ * the problems' states) on first use; the result is back in `pool` when the
+ * stream reaches the end.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA.
+ */
+int swept_batch_naive_advance(swept_batch_t batch, void *pool, void *stream);
+
 /* Synchronise `stream` and return the device status of the last advance:
  * SWEPT_OK or SWEPT_ETIMEOUT. */
 int swept_batch_status(swept_batch_t batch, void *stream);

@@ -32,7 +32,7 @@ EXPORTS = (
     "swept_f32c_split", "swept_f32c_merge", "swept_reduce", "swept_strerror", "swept_version",
     "swept_advance_noalloc", "swept_plan_set",
     "swept_batch_plan", "swept_batch_set", "swept_batch_info", "swept_advance_batch",
-    "swept_batch_status", "swept_batch_destroy", "swept_adjoint",
+    "swept_batch_status", "swept_batch_destroy", "swept_adjoint", "swept_batch_naive_advance",
 )
 
 SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH = 0, 1, 2, 3
@@ -94,6 +94,8 @@ def load(path: str | None = None):
         L.swept_batch_info.restype = i32
         L.swept_advance_batch.argtypes = [vp, vp, vp]
         L.swept_advance_batch.restype = i32
+        L.swept_batch_naive_advance.argtypes = [vp, vp, vp]
+        L.swept_batch_naive_advance.restype = i32
         L.swept_batch_status.argtypes = [vp, vp]
         L.swept_batch_status.restype = i32
         L.swept_batch_destroy.argtypes = [vp]
@@ -320,6 +322,13 @@ def swept_advance_batch(batch: Batch, pool, stream=None):
     """Advance every problem of the batch in ``pool`` (a CUDA tensor of pool_bytes bytes)."""
     _check(load().swept_advance_batch(batch.handle, _dev_ptr(pool, batch.pool_bytes, "pool"),
                                       _stream(stream)), "swept_advance_batch")
+    return pool
+
+
+def swept_batch_naive_advance(batch: Batch, pool, stream=None):
+    """Same result by one launch per time step over the problems still active (baseline)."""
+    _check(load().swept_batch_naive_advance(batch.handle, _dev_ptr(pool, batch.pool_bytes, "pool"),
+                                            _stream(stream)), "swept_batch_naive_advance")
     return pool
 
 

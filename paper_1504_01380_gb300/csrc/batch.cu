@@ -234,6 +234,116 @@ cudaError_t launch_batch(int dtype, int KH, int KK, const BatchArgs& ba, int gri
                             : launch_batch_dt<F32C>(KH, KK, ba, grid, s, query, cap);
 }
 
+// ---------------------------------------------------------------------------
+// Naive batched stepper: the stronger per-step baseline for a batch.  One
+// launch per time step covers every problem that still has steps left (the
+// problems sorted by step count, descending, so the active ones are a
+// prefix); each thread advances 4 consecutive points of one problem with the
+// same Core as the swept kernels, reading its halo straight from global
+// memory (periodic within its problem).  The state ping-pongs between the
+// pool and a scratch pool of the same layout.
+struct NaiveProb {
+  int64_t u_off, N, nsteps;
+  int stencil;
+  Consts c;
+};
+
+constexpr int kNaiveV = 4;
+constexpr int kNaiveBT = 256;
+
+template <class DT> __device__ __forceinline__ typename DT::C hi_point(const unsigned char* u, int64_t g);
+template <> __device__ __forceinline__ double hi_point<F64>(const unsigned char* u, int64_t g) {
+  return reinterpret_cast<const double*>(u)[g];
+}
+template <> __device__ __forceinline__ float hi_point<F32C>(const unsigned char* u, int64_t g) {
+  return reinterpret_cast<const float*>(u)[g];
+}
+
+// Problem of chunk c: the i with cstart[i] <= c < cstart[i + 1].
+__device__ __forceinline__ int chunk_problem(const int64_t* cstart, int n, int64_t c) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (cstart[mid] <= c) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int ST, class DT>
+__device__ __forceinline__ void naive_points(const NaiveProb& P, const unsigned char* src, unsigned char* dst,
+                                             int64_t g) {
+  constexpr int R = Radius<ST>::value;
+  using Cc = typename DT::C;
+  const unsigned char* u = src + P.u_off;
+  Tile<DT, kNaiveV> t;
+  load_points<kNaiveV>(t, u, P.N, g);
+  Cc x[kNaiveV + 2 * R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int64_t gl = g - R + i;
+    if (gl < 0) gl += P.N;
+    int64_t gr = g + kNaiveV + i;
+    if (gr >= P.N) gr -= P.N;
+    x[i] = hi_point<DT>(u, gl);
+    x[R + kNaiveV + i] = hi_point<DT>(u, gr);
+  }
+#pragma unroll
+  for (int k = 0; k < kNaiveV; ++k) x[R + k] = t.hi(k);
+  Core<ST, DT, kNaiveV>::apply(t, x, P.c);
+  store_points<kNaiveV>(t, dst + P.u_off, P.N, g);
+}
+
+template <class DT>
+__global__ void __launch_bounds__(kNaiveBT)
+batch_naive_kernel(const NaiveProb* __restrict__ probs, const int64_t* __restrict__ cstart, int nact,
+                   const unsigned char* __restrict__ src, unsigned char* __restrict__ dst) {
+  const int64_t c = (int64_t)blockIdx.x * kNaiveBT + threadIdx.x;
+  if (c >= cstart[nact]) return;
+  const int i = chunk_problem(cstart, nact + 1, c);
+  const NaiveProb& P = probs[i];
+  const int64_t g = (c - cstart[i]) * kNaiveV;
+  if (P.stencil == kHeat) naive_points<kHeat, DT>(P, src, dst, g);
+  else naive_points<kKS, DT>(P, src, dst, g);
+}
+
+// Problems whose step count is odd end in the scratch pool: copy their
+// 8N bytes back (one thread per 4 points = 32 bytes).
+__global__ void __launch_bounds__(kNaiveBT)
+batch_copy_odd_kernel(const NaiveProb* __restrict__ probs, const int64_t* __restrict__ cstart, int nprob,
+                      const unsigned char* __restrict__ scratch, unsigned char* __restrict__ pool) {
+  const int64_t c = (int64_t)blockIdx.x * kNaiveBT + threadIdx.x;
+  if (c >= cstart[nprob]) return;
+  const int i = chunk_problem(cstart, nprob + 1, c);
+  const NaiveProb& P = probs[i];
+  if ((P.nsteps & 1) == 0) return;
+  const int64_t byte = P.u_off + (c - cstart[i]) * 32;
+  const uint4* s4 = reinterpret_cast<const uint4*>(scratch + byte);
+  uint4* d4 = reinterpret_cast<uint4*>(pool + byte);
+  d4[0] = s4[0];
+  d4[1] = s4[1];
+}
+
+cudaError_t launch_batch_naive_step(int dtype, const NaiveProb* probs, const int64_t* cstart, int nact,
+                                    int64_t nchunks, const unsigned char* src, unsigned char* dst,
+                                    cudaStream_t s) {
+  const int64_t grid = (nchunks + kNaiveBT - 1) / kNaiveBT;
+  if (grid == 0) return cudaSuccess;
+  if (dtype == SWEPT_F64)
+    batch_naive_kernel<F64><<<(unsigned)grid, kNaiveBT, 0, s>>>(probs, cstart, nact, src, dst);
+  else
+    batch_naive_kernel<F32C><<<(unsigned)grid, kNaiveBT, 0, s>>>(probs, cstart, nact, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_copy_odd(const NaiveProb* probs, const int64_t* cstart, int nprob, int64_t nchunks,
+                                  const unsigned char* scratch, unsigned char* pool, cudaStream_t s) {
+  const int64_t grid = (nchunks + kNaiveBT - 1) / kNaiveBT;
+  if (grid == 0) return cudaSuccess;
+  batch_copy_odd_kernel<<<(unsigned)grid, kNaiveBT, 0, s>>>(probs, cstart, nprob, scratch, pool);
+  return cudaGetLastError();
+}
+
 }  // namespace
 }  // namespace swept
 
@@ -258,6 +368,14 @@ struct swept_batch_s {
   cudaGraphExec_t exec;
   void* graph_pool;
   bool graph_valid;
+  // naive batched stepper: problems by step count (descending), chunk
+  // prefix (4 points per chunk), host copy of the sorted step counts and
+  // of the prefix, scratch pool (allocated on first use)
+  swept::NaiveProb* d_nv;
+  int64_t* d_nv_cstart;
+  int64_t* h_nv_steps;
+  int64_t* h_nv_cstart;
+  unsigned char* nv_scratch;
 };
 
 namespace {
@@ -301,6 +419,11 @@ void free_batch(swept_batch_s* b) {
   cudaFree(b->d_stage_start);
   cudaFree(b->d_counter);
   cudaFree(b->d_status);
+  cudaFree(b->d_nv);
+  cudaFree(b->d_nv_cstart);
+  cudaFree(b->nv_scratch);
+  std::free(b->h_nv_steps);
+  std::free(b->h_nv_cstart);
   std::free(b);
 }
 
@@ -350,7 +473,8 @@ int swept_batch_plan(swept_batch_t* out, int nprob, const swept_problem_t* probs
   if (B_ks == 0) B_ks = 512;
   if ((B_heat != 256 && B_heat != 512) || (B_ks != 256 && B_ks != 512)) return SWEPT_ENOTSUP;
   std::vector<BatchProblem> h(nprob);
-  int64_t e_off = 0, f_off = 0;
+  std::vector<swept::NaiveProb> nv(nprob);
+  int64_t e_off = 0, f_off = 0, extent = 16;
   for (int i = 0; i < nprob; ++i) {
     const swept_problem_t& p = probs[i];
     if (p.stencil != SWEPT_HEAT && p.stencil != SWEPT_KS) return SWEPT_EINVAL;
@@ -375,7 +499,15 @@ int swept_batch_plan(swept_batch_t* out, int nprob, const swept_problem_t* probs
     d.f_off = f_off;
     e_off += (int64_t)d.nwin * 2 * B * 8 * 2;
     f_off += d.nwin;
+    nv[i].u_off = p.offset;
+    nv[i].N = p.N;
+    nv[i].nsteps = p.nsteps;
+    nv[i].stencil = p.stencil;
+    nv[i].c = d.c;
+    extent = std::max<int64_t>(extent, p.offset + 8 * p.N);
   }
+  std::stable_sort(nv.begin(), nv.end(),
+                   [](const swept::NaiveProb& x, const swept::NaiveProb& y) { return x.nsteps > y.nsteps; });
   std::stable_sort(h.begin(), h.end(),
                    [](const BatchProblem& x, const BatchProblem& y) { return x.nstages > y.nstages; });
   const int nstage_max = h[0].nstages;
@@ -401,7 +533,24 @@ int swept_batch_plan(swept_batch_t* out, int nprob, const swept_problem_t* probs
   b->timeout_s = 2.0;
   b->drop_item = -1;
   b->use_graph = 1;
+  b->pool_bytes = extent;
+  b->h_nv_steps = (int64_t*)std::malloc(sizeof(int64_t) * nprob);
+  b->h_nv_cstart = (int64_t*)std::malloc(sizeof(int64_t) * (nprob + 1));
+  if (!b->h_nv_steps || !b->h_nv_cstart) {
+    free_batch(b);
+    return SWEPT_ENOMEM;
+  }
+  b->h_nv_cstart[0] = 0;
+  for (int i = 0; i < nprob; ++i) {
+    b->h_nv_steps[i] = nv[i].nsteps;
+    b->h_nv_cstart[i + 1] = b->h_nv_cstart[i] + nv[i].N / 4;
+  }
   cudaError_t e = cudaMalloc((void**)&b->edges, (size_t)std::max<int64_t>(e_off, 16));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_nv, sizeof(swept::NaiveProb) * nprob);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_nv_cstart, sizeof(int64_t) * (nprob + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_nv, nv.data(), sizeof(swept::NaiveProb) * nprob, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_nv_cstart, b->h_nv_cstart, sizeof(int64_t) * (nprob + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->flags, (size_t)std::max<int64_t>(f_off, 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_probs, sizeof(BatchProblem) * nprob);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_cum, sizeof(int64_t) * (nprob + 1));
@@ -490,6 +639,32 @@ int swept_advance_batch(swept_batch_t b, void* pool, void* stream) {
     b->graph_pool = pool;
   }
   return cuda_status_b(cudaGraphLaunch(b->exec, s));
+}
+
+int swept_batch_naive_advance(swept_batch_t b, void* pool, void* stream) {
+  if (!b || !pool || ((uintptr_t)pool & 15u)) return SWEPT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!b->nv_scratch) {
+    e = cudaMalloc((void**)&b->nv_scratch, (size_t)b->pool_bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->nv_scratch = nullptr;
+      return cuda_status_b(e);
+    }
+  }
+  unsigned char* buf[2] = {static_cast<unsigned char*>(pool), b->nv_scratch};
+  int nact = b->nprob;
+  for (int64_t k = 0; e == cudaSuccess; ++k) {
+    while (nact > 0 && b->h_nv_steps[nact - 1] <= k) --nact;    // active problems: a prefix
+    if (nact == 0) break;
+    e = swept::launch_batch_naive_step(b->dtype, b->d_nv, b->d_nv_cstart, nact, b->h_nv_cstart[nact],
+                                       buf[k & 1], buf[(k + 1) & 1], s);
+  }
+  if (e == cudaSuccess)
+    e = swept::launch_batch_copy_odd(b->d_nv, b->d_nv_cstart, b->nprob, b->h_nv_cstart[b->nprob],
+                                     b->nv_scratch, static_cast<unsigned char*>(pool), s);
+  return cuda_status_b(e);
 }
 
 int swept_batch_status(swept_batch_t b, void* stream) {

@@ -2,8 +2,10 @@
 
 Also: the queue with a single thread block (every dependency waited on),
 a message lost on the host side (one item never publishes) ending in
-SWEPT_ETIMEOUT with the GPU still usable, and the 4096-problem workload
-checked on sampled problems.
+SWEPT_ETIMEOUT with the GPU still usable, the 4096-problem workload
+checked on sampled problems, and the naive batched stepper (one launch per
+step over the active problems) bit-exact against the oracle and the swept
+launch.
 """
 from __future__ import annotations
 
@@ -84,6 +86,26 @@ def test_batch_bit_exact(cuda_lib, dtype, bh, bk):
     assert status == 0
     for (st, n, ns), off, u0 in zip(SMALL, batch.offsets, states):
         assert same(read_state(out, off, n, dtype), expect(st, dtype, u0, ns), dtype), (st, n, ns)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_batch_naive_bit_exact(cuda_lib, dtype):
+    """Per-step stepping over the ragged batch (odd and even step counts, a problem with none)."""
+    import torch
+    sw = cuda_lib
+    states = [workloads.uniform(n, 30 + i) if st == 0 else 10 * workloads.ks_smoothed(n, 30 + i)
+              for i, (st, n, ns) in enumerate(SMALL)]
+    batch = sw.swept_batch_plan([(st, n, ns, prm(st)) for st, n, ns in SMALL], dtype, 256, 512)
+    pool = torch.tensor(build_pool(batch, states, dtype), device="cuda")
+    sw.swept_batch_naive_advance(batch, pool)
+    out = pool.cpu().numpy()
+    for (st, n, ns), off, u0 in zip(SMALL, batch.offsets, states):
+        assert same(read_state(out, off, n, dtype), expect(st, dtype, u0, ns), dtype), (st, n, ns)
+    # the same pool through the swept launch: identical bytes
+    pool2 = torch.tensor(build_pool(batch, states, dtype), device="cuda")
+    sw.swept_advance_batch(batch, pool2)
+    assert sw.swept_batch_status(batch) == 0
+    assert np.array_equal(pool2.cpu().numpy(), out)
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
