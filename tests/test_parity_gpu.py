@@ -252,3 +252,38 @@ def test_graph_replay_bit_exact(cuda_lib, stencil, dtype):
         sw.swept_advance(plan, u, 3 * plan.h + 5)
         torch.cuda.synchronize()
         assert_same(plan, from_device(plan, u), want)
+
+
+def test_max_size_heat_f32c_2p31(cuda_lib):
+    """N = 2^31 points (compensated state 16 GiB, edge buffers 64 GiB; element indices of the lo
+    half beyond 2^31): swept over 2h + 3 sub-timesteps at B = 1024, oracle values at sampled
+    points, including both ends of the array and of the lo half's index range."""
+    import torch
+    sw = cuda_lib
+    N, B = 1 << 31, 1024
+    nsteps = 2 * (B // 2) + 3
+    g = torch.Generator(device="cuda")
+    g.manual_seed(workloads.SEED_BASE + 31)
+    u64 = torch.rand(N, dtype=torch.float64, device="cuda", generator=g).mul_(2.0).sub_(1.0)
+    rng = np.random.default_rng(31)
+    xs = [0, 1, N // 2 - 1, N // 2, N - B, N - 1] + [int(v) for v in rng.integers(0, N, 4)]
+    half = nsteps + 1
+    segs = {}
+    for x in xs:
+        idx = torch.tensor((x + np.arange(-half, half + 1)) % N, device="cuda")
+        segs[x] = u64[idx].cpu().numpy()
+    u = sw.swept_f32c_split(u64)
+    del u64
+    torch.cuda.empty_cache()
+    plan = sw.swept_plan(N, 1, HEAT, [0.25], F32C, B)
+    sw.swept_advance(plan, u, nsteps)
+    torch.cuda.synchronize()
+    for x in xs:
+        hi, lo = oracle.split_f32c(segs[x])
+        hi, lo = oracle.advance_f32c(HEAT, [0.25], hi, lo, nsteps)
+        got_hi = float(u[x].item())
+        got_lo = float(u[N + x].item())
+        assert got_hi == hi[half] and got_lo == lo[half], (x, got_hi, hi[half], got_lo, lo[half])
+    plan.destroy()
+    del u
+    torch.cuda.empty_cache()
