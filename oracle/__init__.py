@@ -7,8 +7,8 @@ this package imports nothing from the product path.
 
 Contents
 --------
-* ``oracle.c`` (compiled here with gcc): per-step FP64 and FP32-compensated
-  steppers, split/merge of the compensated state, the discrete adjoint, the
+* ``oracle.c`` (compiled here with gcc): per-step FP64, plain FP32 and
+  FP32-compensated steppers, split/merge of the compensated state, the discrete adjoint, the
   two-stage Runge-Kutta steppers and the Euler-equations finite-volume
   scheme (Section 7: second-order reconstruction with minmod, Roe spectral
   radius dissipation, midpoint rule; four sub-timesteps per time step), in
@@ -81,11 +81,13 @@ def lib():
             L.oracle_rk2_substep_f64.argtypes = [i32, dp, i32, dp, dp, dp, i64]
             L.oracle_euler_advance.argtypes = [dp, dp, i64, i64]
             L.oracle_euler_advance_f32c.argtypes = [dp, fp, fp, i64, i64]
+            L.oracle_step_f32.argtypes = [i32, dp, fp, fp, i64]
+            L.oracle_advance_f32.argtypes = [i32, dp, fp, i64, i64, i32]
             for f in ("oracle_step_f64", "oracle_advance_f64", "oracle_split_f32c",
                       "oracle_merge_f32c", "oracle_step_f32c", "oracle_advance_f32c",
                       "oracle_adjoint_f64", "oracle_adjoint_step_f64", "oracle_max_threads",
                       "oracle_advance_rk2_f64", "oracle_rk2_substep_f64", "oracle_euler_advance",
-                      "oracle_euler_advance_f32c"):
+                      "oracle_euler_advance_f32c", "oracle_step_f32", "oracle_advance_f32"):
                 getattr(L, f).restype = i32
             _lib = L
         return _lib
@@ -127,6 +129,24 @@ def advance_f64(stencil: int, params, u: np.ndarray, nsteps: int, threads: int =
     p = _params(stencil, params)
     _check(lib().oracle_advance_f64(stencil, _ptr(p), _ptr(u), u.size, int(nsteps), int(threads)),
            "advance_f64")
+    return u
+
+
+def step_f32(stencil: int, params, u: np.ndarray) -> np.ndarray:
+    """One sub-timestep of the plain binary32 scheme (the FP64 expressions in binary32)."""
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    out = np.empty_like(u)
+    p = _params(stencil, params)
+    _check(lib().oracle_step_f32(stencil, _ptr(p), _ptr(u), _ptr(out), u.size), "step_f32")
+    return out
+
+
+def advance_f32(stencil: int, params, u: np.ndarray, nsteps: int, threads: int = 0) -> np.ndarray:
+    """``nsteps`` plain binary32 sub-timesteps (returns a new float32 array)."""
+    u = np.array(u, dtype=np.float32, copy=True, order="C")
+    p = _params(stencil, params)
+    _check(lib().oracle_advance_f32(stencil, _ptr(p), _ptr(u), u.size, int(nsteps), int(threads)),
+           "advance_f32")
     return u
 
 

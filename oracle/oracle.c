@@ -181,6 +181,65 @@ int oracle_advance_f64(int stencil, const double *prm, double *u, int64_t n,
     return OR_OK;
 }
 
+/* ---------------------------------------------------------- plain FP32 -- */
+/*
+ * The FP64 expressions above evaluated in binary32, with the FP32 constants
+ * (a diagnostic precision: what the compensated state below buys):
+ *   heat: s = u[i-1] + u[i+1]; w = s - 2u[i]; u' = fmaf(r32, w, u[i])
+ *   KS:   G, W, D, t as in FP64; u' = fmaf(e32, D, fmaf(b32, W[i], fmaf(a32, t, u[i])))
+ */
+static inline float point_f32(const or_consts *c, const float *u, int64_t i, int64_t n)
+{
+    if (c->stencil == OR_HEAT) {
+        float um = u[wrap(i - 1, n)], u0 = u[i], up = u[wrap(i + 1, n)];
+        float s = um + up;
+        float w = s - 2.0f * u0;
+        return fmaf(c->r32, w, u0);
+    } else {
+        float v[5];
+        for (int k = -2; k <= 2; ++k) v[k + 2] = u[wrap(i + k, n)];
+        float Gm = v[1] * v[1];
+        float Gp = v[3] * v[3];
+        float wm = (v[0] + v[2]) - 2.0f * v[1];
+        float w0 = (v[1] + v[3]) - 2.0f * v[2];
+        float wp = (v[2] + v[4]) - 2.0f * v[3];
+        float D = (wm + wp) - 2.0f * w0;
+        float t = Gp - Gm;
+        return fmaf(c->e32, D, fmaf(c->b32, w0, fmaf(c->a32, t, v[2])));
+    }
+}
+
+int oracle_step_f32(int stencil, const double *prm, const float *u, float *out, int64_t n)
+{
+    or_consts c;
+    if (n <= 0 || make_consts(stencil, prm, &c) != OR_OK) return OR_EINVAL;
+    for (int64_t i = 0; i < n; ++i) out[i] = point_f32(&c, u, i, n);
+    return OR_OK;
+}
+
+int oracle_advance_f32(int stencil, const double *prm, float *u, int64_t n, int64_t nsteps, int nthreads)
+{
+    or_consts c;
+    if (n <= 0 || nsteps < 0 || make_consts(stencil, prm, &c) != OR_OK) return OR_EINVAL;
+    if (nsteps == 0) return OR_OK;
+    float *tmp = (float *)malloc((size_t)n * sizeof(float));
+    if (!tmp) return OR_ENOMEM;
+    float *src = u, *dst = tmp;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int64_t s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) dst[i] = point_f32(&c, src, i, n);
+        float *t = src; src = dst; dst = t;
+    }
+    if (src != u) memcpy(u, src, (size_t)n * sizeof(float));
+    free(tmp);
+    return OR_OK;
+}
+
 /* ------------------------------------------------- FP32 compensated ---- */
 
 static inline void two_sum(float a, float b, float *s, float *err)

@@ -285,6 +285,54 @@ def test_single_step_f32c_ieee_exact(stencil, prm, scale, n):
     assert np.array_equal(ho, eh) and np.array_equal(lout, el)
 
 
+def exact_step32(stencil, prm, u):
+    """The FP64 expressions with every operation rounded to binary32 (rational emulation)."""
+    n = len(u)
+    u = [float(x) for x in u]
+    out = []
+    if stencil == HEAT:
+        r = X.r32(Fraction(prm[0]))
+        for i in range(n):
+            s = X.add32(u[i - 1], u[(i + 1) % n])
+            w = X.sub32(s, X.mul32(2.0, u[i]))
+            out.append(X.fma32(r, w, u[i]))
+    else:
+        a, b, e = (X.r32(Fraction(c)) for c in ks_consts64(*prm))
+        for i in range(n):
+            v = [u[(i + k) % n] for k in range(-2, 3)]
+            Gm, Gp = X.mul32(v[1], v[1]), X.mul32(v[3], v[3])
+            wm = X.sub32(X.add32(v[0], v[2]), X.mul32(2.0, v[1]))
+            w0 = X.sub32(X.add32(v[1], v[3]), X.mul32(2.0, v[2]))
+            wp = X.sub32(X.add32(v[2], v[4]), X.mul32(2.0, v[3]))
+            D = X.sub32(X.add32(wm, wp), X.mul32(2.0, w0))
+            t = X.sub32(Gp, Gm)
+            out.append(X.fma32(e, D, X.fma32(b, w0, X.fma32(a, t, v[2]))))
+    return np.array(out, dtype=np.float32)
+
+
+@pytest.mark.parametrize("stencil,prm,scale", [
+    (HEAT, [0.25], 1.0), (HEAT, [0.1], 1.0), (KS, KS_PRM, 5.0), (KS, (0.0013, 0.7), 5.0)])
+@pytest.mark.parametrize("n", [8, 19, 32])
+def test_single_step_f32_ieee_exact(stencil, prm, scale, n):
+    u = (workloads.uniform(n, 300 + n) * scale).astype(np.float32)
+    assert np.array_equal(oracle.step_f32(stencil, prm, u), exact_step32(stencil, prm, u))
+
+
+def test_plain_f32_error_and_compensation_gain():
+    """Heat, 3000 steps: the plain binary32 scheme stays within its rounding-growth bound of FP64
+    (3000 steps x a few 2^-24 relative), and the compensated state is more than 10x closer."""
+    n, r, nsteps = 4096, 0.25, 3000
+    u0 = workloads.heat_noise_modes(n, 16, 77)
+    ref = oracle.advance_f64(HEAT, [r], u0, nsteps)
+    v = oracle.advance_f32(HEAT, [r], u0.astype(np.float32), nsteps)
+    err_p = np.max(np.abs(v.astype(np.float64) - ref)) / np.max(np.abs(u0))
+    hi, lo = oracle.split_f32c(u0)
+    hi, lo = oracle.advance_f32c(HEAT, [r], hi, lo, nsteps)
+    err_c = np.max(np.abs(oracle.merge_f32c(hi, lo) - ref)) / np.max(np.abs(u0))
+    assert 1e-8 < err_p <= 4 * nsteps * 2.0 ** -24
+    assert err_p > 10 * err_c
+
+
 def test_split_merge_exact():
     u = workloads.uniform(1000, 8) * 1e3
     hi, lo = oracle.split_f32c(u)
