@@ -316,6 +316,20 @@ def run_gpu(args):
     naive_f64 = N_POINTS * NSTEPS / timed64(lambda: sw.swept_naive_advance(plan64, u64, NSTEPS))
     plan64.destroy()
 
+    # plain binary32 state (diagnostic precision): rate and error against the exact solution
+    plan32 = sw.swept_plan(N_POINTS, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32, TILE_B)
+    u32p = u0_dev.float()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    a.record(stream)
+    sw.swept_advance(plan32, u32p, NSTEPS)
+    b.record(stream)
+    torch.cuda.synchronize()
+    swept_f32 = N_POINTS * NSTEPS / (a.elapsed_time(b) / 1e3)
+    err_f32 = float(np.max(np.abs(u32p.double().cpu().numpy() - exact)) / np.max(np.abs(u0)))
+    plan32.destroy()
+    del u32p
+
     # tile sweep B in {64, ..., 1024} (compensated FP32, one step each)
     sweep = {}
     for tb in (64, 128, 256, 512, 1024):
@@ -361,6 +375,7 @@ def run_gpu(args):
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "max_err_vs_exact": max_err,
             "compare": {"naive_f32c": naive_f32c, "swept_f64": swept_f64, "naive_f64": naive_f64,
+                        "swept_f32_plain": swept_f32, "max_err_f32_plain_vs_exact": err_f32,
                         "naive_hbm_roof_16B": naive_roof, "swept_over_naive_hbm_roof": value / world / naive_roof,
                         "ops_per_update": {"f32c_heat": OPS_PER_UPDATE_F32C_HEAT, "f64_heat": OPS_PER_UPDATE_F64_HEAT},
                         "tile_sweep_f32c": sweep},

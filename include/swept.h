@@ -23,6 +23,7 @@
  *   SWEPT_F64  : double u[N].
  *   SWEPT_F32C : float hi[N] followed by float lo[N] (8N bytes); the value
  *                of point i is hi[i] + lo[i] (compensated FP32).
+ *   SWEPT_F32  : float u[N] (4N bytes).
  *   SWEPT_EULER plans: the conserved variables density, momentum, energy.
  *                FP64: double rho[N], m[N], E[N] (24N bytes).  F32C: float
  *                hi of rho, m, E (3N), then lo of rho, m, E (3N) (24N bytes):
@@ -42,6 +43,8 @@ extern "C" {
 /* Arithmetic of the state (Section 2 leaves precision open). */
 #define SWEPT_F64   0   /* IEEE binary64 */
 #define SWEPT_F32C  1   /* binary32 pair (hi, lo), TwoSum-compensated update */
+#define SWEPT_F32   2   /* plain binary32, the FP64 expressions in binary32: a
+                           diagnostic precision (forward-Euler heat and KS)   */
 
 /* Stencils (the sub-timestep of Section 2, one per time level).
  *   SWEPT_HEAT: u_t = u_xx, 3-point forward Euler; radius 1;

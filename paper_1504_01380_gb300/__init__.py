@@ -15,7 +15,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libswept.so")
 
-SWEPT_F64, SWEPT_F32C = 0, 1
+SWEPT_F64, SWEPT_F32C, SWEPT_F32 = 0, 1, 2
 SWEPT_HEAT, SWEPT_KS, SWEPT_HEAT_RK2, SWEPT_KS_RK2, SWEPT_EULER = 0, 1, 2, 3, 4
 SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT = 0, 1, 2
 SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP = 0, -1, -2, -3, -4, -5
@@ -158,7 +158,9 @@ class Plan:
 
     @property
     def state_bytes(self) -> int:
-        return (24 if self.stencil == SWEPT_EULER else 8) * self.N
+        if self.stencil == SWEPT_EULER:
+            return 24 * self.N
+        return (4 if self.dtype == SWEPT_F32 else 8) * self.N
 
     def destroy(self):
         if self._h is not None:
@@ -237,7 +239,8 @@ def swept_reduce(plan: Plan, u, what: int, v=None, out=None, stream=None):
     if out is None:
         out = torch.empty(1, dtype=torch.float64, device=u.device)
     vp = _dev_ptr(v, 8 * plan.N, "v") if v is not None else ctypes.c_void_p(0)
-    _check(load().swept_reduce(plan.handle, _dev_ptr(u, 8 * plan.N, "u"), int(what), vp,
+    _check(load().swept_reduce(plan.handle, _dev_ptr(u, (4 if plan.dtype == SWEPT_F32 else 8) * plan.N, "u"),
+                               int(what), vp,
                                _dev_ptr(out, 8, "out"), _stream(stream)), "swept_reduce")
     return out
 

@@ -87,6 +87,9 @@ cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t
                                  : swept::launch_stage_euler_f32c(p->K, a, s);
   if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_stage_heatrk2_f64(p->K, a, s);
   if (p->stencil == SWEPT_KS_RK2) return swept::launch_stage_ksrk2_f64(p->K, a, s);
+  if (p->dtype == SWEPT_F32)
+    return p->stencil == SWEPT_HEAT ? swept::launch_stage_heat_f32(p->K, a, s)
+                                    : swept::launch_stage_ks_f32(p->K, a, s);
   if (p->stencil == SWEPT_HEAT)
     return p->dtype == SWEPT_F64 ? swept::launch_stage_heat_f64(p->K, a, s)
                                  : swept::launch_stage_heat_f32c(p->K, a, s);
@@ -104,6 +107,9 @@ cudaError_t launch_ring(const swept_plan_s* p, const StageArgs& a, cudaStream_t 
                                  : swept::launch_ring_euler_f32c(p->K, a, w, s);
   if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_ring_heatrk2_f64(p->K, a, w, s);
   if (p->stencil == SWEPT_KS_RK2) return swept::launch_ring_ksrk2_f64(p->K, a, w, s);
+  if (p->dtype == SWEPT_F32)
+    return p->stencil == SWEPT_HEAT ? swept::launch_ring_heat_f32(p->K, a, w, s)
+                                    : swept::launch_ring_ks_f32(p->K, a, w, s);
   if (p->stencil == SWEPT_HEAT)
     return p->dtype == SWEPT_F64 ? swept::launch_ring_heat_f64(p->K, a, w, s)
                                  : swept::launch_ring_heat_f32c(p->K, a, w, s);
@@ -157,9 +163,10 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   const bool euler = stencil_id == SWEPT_EULER;
   const int rad = (stencil_id == SWEPT_HEAT || stencil_id == SWEPT_HEAT_RK2 || euler) ? 1 : 2;
   if (radius != rad) return SWEPT_EINVAL;
-  if (dtype != SWEPT_F64 && dtype != SWEPT_F32C) return SWEPT_EINVAL;
+  if (dtype != SWEPT_F64 && dtype != SWEPT_F32C && dtype != SWEPT_F32) return SWEPT_EINVAL;
   const bool rk2 = stencil_id == SWEPT_HEAT_RK2 || stencil_id == SWEPT_KS_RK2;
   if (rk2 && dtype != SWEPT_F64) return SWEPT_ENOTSUP;
+  if (euler && dtype == SWEPT_F32) return SWEPT_ENOTSUP;
   if (N <= 0) return SWEPT_EINVAL;
   if (B == 0) B = default_B(N, rad, stencil_id, dtype);
   if (B <= 0 || B % 32) return SWEPT_EINVAL;
@@ -189,7 +196,7 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->subs = euler ? 4 : (rk2 ? 2 : 1);
   cudaGetDevice(&p->device);
   const size_t esize = euler ? (dtype == SWEPT_F64 ? sizeof(swept::EulerE) : sizeof(swept::EulerEF))
-                              : (rk2 ? 16 : 8);
+                              : (rk2 ? 16 : (dtype == SWEPT_F32 ? 4 : 8));
   p->edge_half = (size_t)p->nwin * 2 * B * esize;
   cudaError_t e = cudaMalloc((void**)&p->edges, 2 * p->edge_half);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->red, 2 * swept::kReduceBlocks * sizeof(double));
@@ -492,7 +499,7 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     cur ^= 1;
   }
   if (e == cudaSuccess && cur == 1) {
-    const size_t bytes = (size_t)p->N * 8;   // F64: N doubles; F32C: 2N floats
+    const size_t bytes = (size_t)p->N * (p->dtype == SWEPT_F32 ? 4 : 8);   // F64, F32C: 8 B per point
     e = cudaMemcpyAsync(u, p->edges, bytes, cudaMemcpyDeviceToDevice, s);
   }
   return cuda_status(e);

@@ -58,6 +58,9 @@ template <> __device__ __forceinline__ double value_at<1>(const void* u, int64_t
   const float* f = static_cast<const float*>(u);
   return __dadd_rn((double)f[i], (double)f[N + i]);
 }
+template <> __device__ __forceinline__ double value_at<2>(const void* u, int64_t, int64_t i) {
+  return (double)static_cast<const float*>(u)[i];
+}
 
 __device__ __forceinline__ void block_reduce(Acc& acc, double* sh_s, double* sh_c) {
   const int tid = threadIdx.x;
@@ -138,6 +141,11 @@ cudaError_t launch_reduce(int dtype, const void* u, int what, const double* v, i
     if (what == 0) return reduce_t<0, 0>(u, v, N, scratch, out, s);
     if (what == 1) return reduce_t<0, 1>(u, v, N, scratch, out, s);
     return reduce_t<0, 2>(u, v, N, scratch, out, s);
+  }
+  if (dtype == 2) {
+    if (what == 0) return reduce_t<2, 0>(u, v, N, scratch, out, s);
+    if (what == 1) return reduce_t<2, 1>(u, v, N, scratch, out, s);
+    return reduce_t<2, 2>(u, v, N, scratch, out, s);
   }
   if (what == 0) return reduce_t<1, 0>(u, v, N, scratch, out, s);
   if (what == 1) return reduce_t<1, 1>(u, v, N, scratch, out, s);

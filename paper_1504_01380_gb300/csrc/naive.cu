@@ -24,6 +24,9 @@ template <> __device__ __forceinline__ double hi_at<F64>(const void* u, int64_t 
 template <> __device__ __forceinline__ float hi_at<F32C>(const void* u, int64_t g) {
   return static_cast<const float*>(u)[g];
 }
+template <> __device__ __forceinline__ float hi_at<F32>(const void* u, int64_t g) {
+  return static_cast<const float*>(u)[g];
+}
 
 template <int ST, class DT>
 __global__ void __launch_bounds__(kNaiveThreads)
@@ -224,8 +227,11 @@ cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double
 cudaError_t launch_naive_step(int stencil, int dtype, const void* in, void* out, int64_t N,
                               const Consts& c, cudaStream_t s) {
   if (N % kV) return cudaErrorInvalidValue;
-  if (stencil == kHeat) return dtype == 0 ? launch<kHeat, F64>(in, out, N, c, s)
-                                          : launch<kHeat, F32C>(in, out, N, c, s);
+  if (stencil == kHeat) {
+    if (dtype == 2) return launch<kHeat, F32>(in, out, N, c, s);
+    return dtype == 0 ? launch<kHeat, F64>(in, out, N, c, s) : launch<kHeat, F32C>(in, out, N, c, s);
+  }
+  if (dtype == 2) return launch<kKS, F32>(in, out, N, c, s);
   return dtype == 0 ? launch<kKS, F64>(in, out, N, c, s) : launch<kKS, F32C>(in, out, N, c, s);
 }
 

@@ -13,7 +13,7 @@ constexpr int kWarpsPerBlock = 4;
 
 // Arguments of one swept stage launch (one window per warp).
 struct StageArgs {
-  void* u;             // flat state (F64 double[N]; F32C float hi[N], lo[N])
+  void* u;             // flat state (F64 double[N]; F32C float hi[N], lo[N]; F32 float[N])
   const void* ein;     // leading edges of the previous stage: nwin * 2B elements
   void* eout;          // leading edges written by this stage
   int64_t N;
@@ -36,12 +36,16 @@ cudaError_t launch_stage_heat_f64(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_heat_f32c(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_ks_f64(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_ks_f32c(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_heat_f32(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_stage_ks_f32(int K, const StageArgs& a, cudaStream_t s);
 
 // Ring-pipelined full-diamond stage (hv = ht = h); nwarps <= 0 picks a size.
 cudaError_t launch_ring_heat_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 cudaError_t launch_ring_heat_f32c(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 cudaError_t launch_ring_ks_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 cudaError_t launch_ring_ks_f32c(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+cudaError_t launch_ring_heat_f32(int K, const StageArgs& a, int nwarps, cudaStream_t s);
+cudaError_t launch_ring_ks_f32(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 
 // Adjoint (transposed KS, FP64) stage over a tape.
 cudaError_t launch_stage_ksadj_f64(int K, const StageArgs& a, cudaStream_t s);

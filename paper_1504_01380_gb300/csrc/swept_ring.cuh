@@ -108,7 +108,7 @@ struct RingImpl {
                                                    int lane) {
     const uint4* s4 = reinterpret_cast<const uint4*>(src);
     uint4* d4 = reinterpret_cast<uint4*>(dst);
-    const int n16 = n * (int)sizeof(E) / 16;
+    const int n16 = (n * (int)sizeof(E) + 15) / 16;   // rounded up: slots hold B elements
     for (int i = lane; i < n16; i += 32) d4[i] = s4[i];
   }
 

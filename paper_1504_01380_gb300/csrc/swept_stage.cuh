@@ -196,12 +196,13 @@ struct StageImpl {
     }
   }
 
-  // Copy n elements (n * sizeof(E) a multiple of 16, 16-byte aligned) with the warp.
+  // Copy n elements with the warp in 16-byte units (16-byte aligned; a plain
+  // FP32 count is rounded up to 4 elements, which stays inside the B-element slot).
   static __device__ __forceinline__ void warp_copy(E* __restrict__ dst, const E* __restrict__ src,
                                                    int n, int lane) {
     const uint4* s4 = reinterpret_cast<const uint4*>(src);
     uint4* d4 = reinterpret_cast<uint4*>(dst);
-    const int n16 = n * (int)sizeof(E) / 16;
+    const int n16 = (n * (int)sizeof(E) + 15) / 16;   // rounded up: slots hold B elements
     for (int i = lane; i < n16; i += 32) d4[i] = s4[i];
   }
 

@@ -66,6 +66,8 @@ def _plan_rc(lib, N, radius, stencil, params, dtype, B):
     (1024, 2, 1, [0.002, 0.0], 0, 64, -1),  # dx must be positive
     (1024, 2, 1, [0.002], 0, 64, -1),       # KS needs two parameters
     (1024, 1, 4, [1e-4, 1e-3, 1.4], 1, 512, -5),  # compensated Euler: B <= 256
+    (1024, 1, 4, [1e-4, 1e-3, 1.4], 2, 64, -5),   # plain FP32: forward-Euler heat and KS only
+    (1024, 1, 2, [0.25], 2, 64, -5),              # plain FP32: no Runge-Kutta
     (1024, 1, 4, [1e-4, 1e-3, 1.4], 0, 256, -5),  # FP64 Euler: B <= 128
     (1024, 2, 4, [1e-4, 1e-3, 1.4], 0, 32, -1),   # Euler radius is 1
     (1024, 1, 4, [1e-4, 1e-3], 0, 32, -1),        # Euler needs {dt, dx, gamma}

@@ -1,10 +1,10 @@
 """GPU parity: the CUDA swept and naive steppers against the CPU oracle.
 
 Every comparison goes through the C ABI (the Python binding marshals only).
-FP64 and FP32-compensated results must be bit-exact against the oracle's
-per-step stepping of the same arithmetic (the swept rule only reorders the
-work); the compensated state is also compared with the FP64 oracle within a
-stated tolerance.
+FP64, FP32-compensated and plain FP32 results must be bit-exact against the
+oracle's per-step stepping of the same arithmetic (the swept rule only
+reorders the work); the compensated state is also compared with the FP64
+oracle within a stated tolerance.
 """
 from __future__ import annotations
 
@@ -18,7 +18,7 @@ from oracle import reductions as ored
 pytestmark = pytest.mark.gpu
 
 HEAT, KS = 0, 1
-F64, F32C = 0, 1
+F64, F32C, F32 = 0, 1, 2
 KS_PRM = (workloads.KS_DT, workloads.KS_DX)
 EPS = np.finfo(np.float64).eps
 
@@ -35,13 +35,15 @@ def to_device(sw, plan, u0):
     import torch
     if plan.dtype == F64:
         return torch.tensor(u0, dtype=torch.float64, device="cuda")
+    if plan.dtype == F32:
+        return torch.tensor(u0.astype(np.float32), device="cuda")
     hi, lo = oracle.split_f32c(u0)
     return torch.tensor(np.concatenate([hi, lo]), dtype=torch.float32, device="cuda")
 
 
 def from_device(plan, t):
     a = t.cpu().numpy()
-    if plan.dtype == F64:
+    if plan.dtype in (F64, F32):
         return a
     return a[: plan.N], a[plan.N:]
 
@@ -49,12 +51,14 @@ def from_device(plan, t):
 def oracle_run(stencil, dtype, u0, nsteps, threads=0):
     if dtype == F64:
         return oracle.advance_f64(stencil, params_of(stencil), u0, nsteps, threads)
+    if dtype == F32:
+        return oracle.advance_f32(stencil, params_of(stencil), u0.astype(np.float32), nsteps, threads)
     hi, lo = oracle.split_f32c(u0)
     return oracle.advance_f32c(stencil, params_of(stencil), hi, lo, nsteps, threads)
 
 
 def assert_same(plan, got, want):
-    if plan.dtype == F64:
+    if plan.dtype in (F64, F32):
         bad = np.flatnonzero(got != want)
         assert bad.size == 0, f"{bad.size} points differ, first at {bad[:5]}"
     else:
@@ -71,7 +75,7 @@ def run_gpu(sw, plan, u0, nsteps, naive=False):
     return from_device(plan, u)
 
 
-CASES = [(st, dt, B) for st in (HEAT, KS) for dt in (F64, F32C) for B in (32, 64, 128, 256, 512, 1024)
+CASES = [(st, dt, B) for st in (HEAT, KS) for dt in (F64, F32C, F32) for B in (32, 64, 128, 256, 512, 1024)
          if (B // 32) % (1 if st == HEAT else 2) == 0]
 
 
@@ -90,7 +94,7 @@ def test_swept_bit_exact_vs_oracle(cuda_lib, stencil, dtype, B):
         assert_same(plan, got, oracle_run(stencil, dtype, u0, nsteps))
 
 
-@pytest.mark.parametrize("stencil,dtype", [(s, d) for s in (HEAT, KS) for d in (F64, F32C)])
+@pytest.mark.parametrize("stencil,dtype", [(s, d) for s in (HEAT, KS) for d in (F64, F32C, F32)])
 def test_naive_bit_exact_vs_oracle(cuda_lib, stencil, dtype):
     sw = cuda_lib
     r = 1 if stencil == HEAT else 2
@@ -102,7 +106,7 @@ def test_naive_bit_exact_vs_oracle(cuda_lib, stencil, dtype):
                     oracle_run(stencil, dtype, u0, nsteps))
 
 
-@pytest.mark.parametrize("stencil,dtype", [(s, d) for s in (HEAT, KS) for d in (F64, F32C)])
+@pytest.mark.parametrize("stencil,dtype", [(s, d) for s in (HEAT, KS) for d in (F64, F32C, F32)])
 def test_single_window_is_its_own_neighbour(cuda_lib, stencil, dtype):
     sw = cuda_lib
     r = 1 if stencil == HEAT else 2
@@ -148,7 +152,7 @@ def test_split_merge_bit_exact(cuda_lib):
     assert np.array_equal(m, oracle.merge_f32c(hi, lo))
 
 
-@pytest.mark.parametrize("dtype", [F64, F32C])
+@pytest.mark.parametrize("dtype", [F64, F32C, F32])
 def test_reductions(cuda_lib, dtype):
     import torch
     sw = cuda_lib
@@ -157,7 +161,8 @@ def test_reductions(cuda_lib, dtype):
     u0 = workloads.heat_noise_modes(N, 16, 4)
     v = workloads.uniform(N, 5)
     u = to_device(sw, plan, u0)
-    vals = u0 if dtype == F64 else oracle.merge_f32c(*oracle.split_f32c(u0))
+    vals = {F64: u0, F32: u0.astype(np.float32).astype(np.float64),
+            F32C: oracle.merge_f32c(*oracle.split_f32c(u0))}[dtype]
     vt = torch.tensor(v, device="cuda")
     got_sum = sw.swept_reduce(plan, u, sw.SWEPT_SUM).item()
     got_j = sw.swept_reduce(plan, u, sw.SWEPT_HALF_SUMSQ).item()
