@@ -687,6 +687,19 @@ def run_latency_workload(args):
     with torch.cuda.graph(g):
         sw.swept_naive_advance(plan, u, nsteps)
     naive_graph = per_sub(g.replay, reps=3)
+    # the same without programmatic dependent launches (plain kernel boundaries)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_PDL, 0)
+    g2 = torch.cuda.CUDAGraph()
+    u.copy_(u0)
+    with torch.cuda.graph(g2):
+        sw.swept_naive_advance(plan, u, nsteps)
+    naive_graph_nopdl = per_sub(g2.replay, reps=3)
+    plan.destroy()
+    plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, 32)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_PDL, 0)
+    swept_graph_nopdl = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
+    plan.destroy()
     fit = tune.fit_eq1([(int(b), t) for b, t in swept_graph.items()])
     best = min(swept_graph, key=swept_graph.get)
     line = {"metric": "time per sub-timestep (latency regime)", "value": swept_graph[best] * 1e9,
@@ -696,6 +709,7 @@ def run_latency_workload(args):
             "swept_ns": {b: t * 1e9 for b, t in swept.items()},
             "swept_graph_ns": {b: t * 1e9 for b, t in swept_graph.items()},
             "naive_ns": naive * 1e9, "naive_graph_ns": naive_graph * 1e9,
+            "without_pdl": {"swept_graph_ns_B32": swept_graph_nopdl * 1e9, "naive_graph_ns": naive_graph_nopdl * 1e9},
             "speedup_vs_naive": naive / swept_graph[best],
             "speedup_vs_naive_graph": naive_graph / swept_graph[best],
             "eq1_fit": {"s_ns": fit["s"] * 1e9, "tau_ns": fit["tau"] * 1e9,

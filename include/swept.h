@@ -142,11 +142,17 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        and replays it afterwards (fewer host launches: the
  *                        GPU's counterpart of the latency tau of Section 4);
  *                        0 (default): launch the stages directly.
+ *   SWEPT_OPT_PDL        1 (default): consecutive kernels of an advance (stages;
+ *                        the naive stepper's steps) are programmatic dependent
+ *                        launches: the next kernel is scheduled while the
+ *                        previous one runs and waits for its results on the
+ *                        device, hiding the launch gap; 0: plain launches.
  * Errors: SWEPT_EINVAL for an unknown option or value.
  */
 #define SWEPT_OPT_DIAMOND     0
 #define SWEPT_OPT_RING_WARPS  1
 #define SWEPT_OPT_GRAPH       2
+#define SWEPT_OPT_PDL         3
 #define SWEPT_DIAMOND_AUTO    0
 #define SWEPT_DIAMOND_WINDOW  1
 #define SWEPT_DIAMOND_RING    2

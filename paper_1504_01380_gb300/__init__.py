@@ -21,7 +21,7 @@ SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT = 0, 1, 2
 SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP = 0, -1, -2, -3, -4, -5
 SWEPT_ETOOBIG = -6
 SWEPT_NOALLOC_MAX_N = 1 << 20
-SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS, SWEPT_OPT_GRAPH = 0, 1, 2
+SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS, SWEPT_OPT_GRAPH, SWEPT_OPT_PDL = 0, 1, 2, 3
 SWEPT_DIAMOND_AUTO, SWEPT_DIAMOND_WINDOW, SWEPT_DIAMOND_RING = 0, 1, 2
 
 RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2, SWEPT_HEAT_RK2: 1, SWEPT_KS_RK2: 2, SWEPT_EULER: 1}

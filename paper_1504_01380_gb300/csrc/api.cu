@@ -29,6 +29,7 @@ struct swept_plan_s {
   int rk2;                // two-stage Runge-Kutta: 2 levels per step, pair edges
   int subs;               // sub-timesteps (levels) per time step: 1, 2 or 4
   int use_graph;          // replay the stage sequence as a CUDA graph
+  int pdl;                // programmatic dependent launch between consecutive kernels
   cudaGraphExec_t gexec;  // captured advance (valid for g_u, g_nsteps)
   void* g_u;
   int64_t g_nsteps;
@@ -194,6 +195,7 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->c = c;
   p->rk2 = rk2 ? 1 : 0;
   p->subs = euler ? 4 : (rk2 ? 2 : 1);
+  p->pdl = 1;
   cudaGetDevice(&p->device);
   const size_t esize = euler ? (dtype == SWEPT_F64 ? sizeof(swept::EulerE) : sizeof(swept::EulerEF))
                               : (rk2 ? 16 : (dtype == SWEPT_F32 ? 4 : 8));
@@ -242,6 +244,19 @@ int swept_plan_set(swept_plan_t p, int option, int64_t value) {
   if (option == SWEPT_OPT_GRAPH) {
     if (value != 0 && value != 1) return SWEPT_EINVAL;
     p->use_graph = (int)value;
+    if (p->g_valid) {              // the captured launches carry the old setting
+      cudaGraphExecDestroy(p->gexec);
+      p->g_valid = 0;
+    }
+    return SWEPT_OK;
+  }
+  if (option == SWEPT_OPT_PDL) {
+    if (value != 0 && value != 1) return SWEPT_EINVAL;
+    p->pdl = (int)value;
+    if (p->g_valid) {
+      cudaGraphExecDestroy(p->gexec);
+      p->g_valid = 0;
+    }
     return SWEPT_OK;
   }
   return SWEPT_EINVAL;
@@ -263,6 +278,7 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
   a.N = p->N;
   a.nwin = p->nwin;
   a.c = p->c;
+  a.pdl = p->pdl;
   // stage k: windows shifted by B/2 when k is odd (the alternating point
   // sets of Section 3); reads the edges of stage k-1, writes its own.
   const bool ring = use_ring(p);
@@ -348,6 +364,7 @@ cudaError_t adjoint_sweep(swept_plan_s* p, double* lam, int64_t len, const doubl
   a.c = p->c;
   a.tape = tape;
   a.tape_len = len;
+  a.pdl = p->pdl;
   auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
     a.offset = (k & 1) ? p->B / 2 : 0;
     a.hv = hv;
@@ -427,7 +444,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
     e = cudaMemcpyAsync(tape, ckpt + g * p->N, bytes, cudaMemcpyDeviceToDevice, s);
     for (int64_t n = 1; n < len && e == cudaSuccess; ++n)
       e = swept::launch_naive_step(p->stencil, p->dtype, tape + (n - 1) * p->N, tape + n * p->N, p->N,
-                                   p->c, s);
+                                   p->c, s, p->pdl != 0);
     if (e == cudaSuccess) e = adjoint_sweep(p, lam, len, tape, s);
   }
   return cuda_status(e);
@@ -448,9 +465,10 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
       const float* hi = bufs[cur];
       const float* lo = bufs[cur] + 3 * N;
-      e = swept::launch_naive_euler_f32c(0, hi, hi, lo, qm, nullptr, N, ch, g1, s);
+      e = swept::launch_naive_euler_f32c(0, hi, hi, lo, qm, nullptr, N, ch, g1, s, p->pdl != 0);
       if (e == cudaSuccess)
-        e = swept::launch_naive_euler_f32c(1, qm, hi, lo, bufs[cur ^ 1], bufs[cur ^ 1] + 3 * N, N, cf, g1, s);
+        e = swept::launch_naive_euler_f32c(1, qm, hi, lo, bufs[cur ^ 1], bufs[cur ^ 1] + 3 * N, N, cf, g1, s,
+                                           p->pdl != 0);
       cur ^= 1;
     }
     if (e == cudaSuccess && cur == 1)
@@ -467,9 +485,9 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     cudaError_t e = cudaSuccess;
     int cur = 0;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-      e = swept::launch_naive_euler(bufs[cur], bufs[cur], qm, N, half, p->c.g1, s);
+      e = swept::launch_naive_euler(bufs[cur], bufs[cur], qm, N, half, p->c.g1, s, p->pdl != 0);
       if (e == cudaSuccess)
-        e = swept::launch_naive_euler(qm, bufs[cur], bufs[cur ^ 1], N, p->c.dtdx, p->c.g1, s);
+        e = swept::launch_naive_euler(qm, bufs[cur], bufs[cur ^ 1], N, p->c.dtdx, p->c.g1, s, p->pdl != 0);
       cur ^= 1;
     }
     if (e == cudaSuccess && cur == 1)
@@ -483,8 +501,9 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     cudaError_t e = cudaSuccess;
     int cur = 0;
     for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-      e = swept::launch_naive_rk2(p->stencil, 0, bufs[cur], nullptr, m, p->N, p->c, s);
-      if (e == cudaSuccess) e = swept::launch_naive_rk2(p->stencil, 1, bufs[cur], m, bufs[cur ^ 1], p->N, p->c, s);
+      e = swept::launch_naive_rk2(p->stencil, 0, bufs[cur], nullptr, m, p->N, p->c, s, p->pdl != 0);
+      if (e == cudaSuccess)
+        e = swept::launch_naive_rk2(p->stencil, 1, bufs[cur], m, bufs[cur ^ 1], p->N, p->c, s, p->pdl != 0);
       cur ^= 1;
     }
     if (e == cudaSuccess && cur == 1)
@@ -495,7 +514,7 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   cudaError_t e = cudaSuccess;
   int cur = 0;
   for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
-    e = swept::launch_naive_step(p->stencil, p->dtype, bufs[cur], bufs[cur ^ 1], p->N, p->c, s);
+    e = swept::launch_naive_step(p->stencil, p->dtype, bufs[cur], bufs[cur ^ 1], p->N, p->c, s, p->pdl != 0);
     cur ^= 1;
   }
   if (e == cudaSuccess && cur == 1) {

@@ -32,6 +32,7 @@ template <int ST, class DT>
 __global__ void __launch_bounds__(kNaiveThreads)
 naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N, const Consts c) {
   constexpr int R = Radius<ST>::value;
+  griddep_wait_and_release();
   using Cc = typename DT::C;
   const int lane = threadIdx.x & 31;
   const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
@@ -69,11 +70,11 @@ naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N
 }
 
 template <int ST, class DT>
-cudaError_t launch(const void* in, void* out, int64_t N, const Consts& c, cudaStream_t s) {
+cudaError_t launch(const void* in, void* out, int64_t N, const Consts& c, cudaStream_t s, bool pdl) {
   const int64_t threads = N / kV;
   const int64_t grid = (threads + kNaiveThreads - 1) / kNaiveThreads;
-  naive_step_kernel<ST, DT><<<(unsigned)grid, kNaiveThreads, 0, s>>>(in, out, N, c);
-  return cudaGetLastError();
+  return launch_kernel(pdl, naive_step_kernel<ST, DT>, dim3((unsigned)grid), dim3(kNaiveThreads), 0, s, in, out,
+                       N, c);
 }
 
 // Runge-Kutta sub-timestep on the whole field: sub 0 writes m = A(u) to out,
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(kNaiveThreads)
 naive_rk2_kernel(int sub, const double* __restrict__ u, const double* __restrict__ m,
                  double* __restrict__ out, int64_t N, const Consts c) {
   constexpr int R = Radius<ST>::value;
+  griddep_wait_and_release();
   const int lane = threadIdx.x & 31;
   const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
   const bool valid = i0 < N;
@@ -141,6 +143,7 @@ naive_euler_kernel(const T* __restrict__ arg, const T* __restrict__ base, const 
                    T* __restrict__ out, T* __restrict__ out_lo, int64_t N, T ca, T g1) {
   using O = EOps<T>;
   __shared__ T sa[3][kEulerT + 3], ss[3][kEulerT + 1], sf[3][kEulerT];
+  griddep_wait_and_release();
   const int64_t b0 = (int64_t)blockIdx.x * (kEulerT - 1);
   for (int j = threadIdx.x; j < kEulerT + 3; j += kEulerT) {
     int64_t g = (b0 - 2 + j) % N;
@@ -195,44 +198,44 @@ naive_euler_kernel(const T* __restrict__ arg, const T* __restrict__ base, const 
 }  // namespace
 
 cudaError_t launch_naive_euler(const double* arg, const double* base, double* out, int64_t N, double ca,
-                               double g1, cudaStream_t s) {
+                               double g1, cudaStream_t s, bool pdl) {
   if (N <= 0) return cudaErrorInvalidValue;
   const int64_t grid = (N + kEulerT - 2) / (kEulerT - 1);
-  naive_euler_kernel<double, 0><<<(unsigned)grid, kEulerT, 0, s>>>(arg, base, nullptr, out, nullptr, N, ca, g1);
-  return cudaGetLastError();
+  return launch_kernel(pdl, naive_euler_kernel<double, 0>, dim3((unsigned)grid), dim3(kEulerT), 0, s, arg, base,
+                       (const double*)nullptr, out, (double*)nullptr, N, ca, g1);
 }
 
 cudaError_t launch_naive_euler_f32c(int full, const float* arg, const float* hi, const float* lo, float* out,
-                                    float* out_lo, int64_t N, float ca, float g1, cudaStream_t s) {
+                                    float* out_lo, int64_t N, float ca, float g1, cudaStream_t s, bool pdl) {
   if (N <= 0) return cudaErrorInvalidValue;
   const int64_t grid = (N + kEulerT - 2) / (kEulerT - 1);
   if (full)
-    naive_euler_kernel<float, 2><<<(unsigned)grid, kEulerT, 0, s>>>(arg, hi, lo, out, out_lo, N, ca, g1);
-  else
-    naive_euler_kernel<float, 1><<<(unsigned)grid, kEulerT, 0, s>>>(arg, hi, lo, out, nullptr, N, ca, g1);
-  return cudaGetLastError();
+    return launch_kernel(pdl, naive_euler_kernel<float, 2>, dim3((unsigned)grid), dim3(kEulerT), 0, s, arg, hi, lo,
+                         out, out_lo, N, ca, g1);
+  return launch_kernel(pdl, naive_euler_kernel<float, 1>, dim3((unsigned)grid), dim3(kEulerT), 0, s, arg, hi, lo,
+                       out, (float*)nullptr, N, ca, g1);
 }
 
 cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
-                             const Consts& c, cudaStream_t s) {
+                             const Consts& c, cudaStream_t s, bool pdl) {
   if (N % kV) return cudaErrorInvalidValue;
   const int64_t grid = (N / kV + kNaiveThreads - 1) / kNaiveThreads;
   if (stencil == 2)
-    naive_rk2_kernel<kHeatRK2><<<(unsigned)grid, kNaiveThreads, 0, s>>>(sub, u, m, out, N, c);
-  else
-    naive_rk2_kernel<kKSRK2><<<(unsigned)grid, kNaiveThreads, 0, s>>>(sub, u, m, out, N, c);
-  return cudaGetLastError();
+    return launch_kernel(pdl, naive_rk2_kernel<kHeatRK2>, dim3((unsigned)grid), dim3(kNaiveThreads), 0, s, sub, u,
+                         m, out, N, c);
+  return launch_kernel(pdl, naive_rk2_kernel<kKSRK2>, dim3((unsigned)grid), dim3(kNaiveThreads), 0, s, sub, u, m,
+                       out, N, c);
 }
 
 cudaError_t launch_naive_step(int stencil, int dtype, const void* in, void* out, int64_t N,
-                              const Consts& c, cudaStream_t s) {
+                              const Consts& c, cudaStream_t s, bool pdl) {
   if (N % kV) return cudaErrorInvalidValue;
   if (stencil == kHeat) {
-    if (dtype == 2) return launch<kHeat, F32>(in, out, N, c, s);
-    return dtype == 0 ? launch<kHeat, F64>(in, out, N, c, s) : launch<kHeat, F32C>(in, out, N, c, s);
+    if (dtype == 2) return launch<kHeat, F32>(in, out, N, c, s, pdl);
+    return dtype == 0 ? launch<kHeat, F64>(in, out, N, c, s, pdl) : launch<kHeat, F32C>(in, out, N, c, s, pdl);
   }
-  if (dtype == 2) return launch<kKS, F32>(in, out, N, c, s);
-  return dtype == 0 ? launch<kKS, F64>(in, out, N, c, s) : launch<kKS, F32C>(in, out, N, c, s);
+  if (dtype == 2) return launch<kKS, F32>(in, out, N, c, s, pdl);
+  return dtype == 0 ? launch<kKS, F64>(in, out, N, c, s, pdl) : launch<kKS, F32C>(in, out, N, c, s, pdl);
 }
 
 }  // namespace swept

@@ -29,7 +29,31 @@ struct StageArgs {
   const double* tape;
   int64_t tape_len;
   int64_t lev_fill, lev_trap;
+  int pdl;             // launch with programmatic dependent launch (host side only)
 };
+
+// Launch `kern` on `s`; with pdl, as a programmatic dependent launch (the
+// kernel may be scheduled while the previous kernel on the stream runs, and
+// waits for it in griddep_wait_and_release).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_kernel(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t s, Args... args) {
+  if (!pdl) {
+    kern<<<grid, block, smem, s>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 // Launchers, one per (stencil, dtype); K = B / 32.
 cudaError_t launch_stage_heat_f64(int K, const StageArgs& a, cudaStream_t s);
@@ -65,15 +89,16 @@ cudaError_t launch_ring_euler_f32c(int K, const StageArgs& a, int nwarps, cudaSt
 // Naive Euler stage of the midpoint rule on the planar state: out = base -
 // ca (F_{i+1/2} - F_{i-1/2}) with the fluxes of (arg, minmod slopes of arg).
 cudaError_t launch_naive_euler(const double* arg, const double* base, double* out, int64_t N, double ca,
-                               double g1, cudaStream_t s);
+                               double g1, cudaStream_t s, bool pdl = false);
 // Compensated FP32 version: full = 0: out = hi + fma(-ca, dF, lo) (the
 // midpoint, from arg = hi); full = 1: (out, out_lo) = TwoSum(hi, fma(-ca, dF, lo))
 // (from arg = the midpoint).  All arrays 3N floats, planar.
 cudaError_t launch_naive_euler_f32c(int full, const float* arg, const float* hi, const float* lo, float* out,
-                                    float* out_lo, int64_t N, float ca, float g1, cudaStream_t s);
+                                    float* out_lo, int64_t N, float ca, float g1, cudaStream_t s,
+                                    bool pdl = false);
 // Naive Runge-Kutta sub-timestep: sub 0: m = A(u); sub 1: out = B(u, m).
 cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
-                             const Consts& c, cudaStream_t s);
+                             const Consts& c, cudaStream_t s, bool pdl = false);
 
 // Shared-memory bytes per block of the stage kernel for tile width B and
 // edge elements of esize bytes (8; 16 for the Runge-Kutta pair; 72 or 48
@@ -82,7 +107,7 @@ inline size_t stage_smem_bytes(int B, int esize = 8) { return (size_t)kWarpsPerB
 
 // Naive per-step stepper: out = S(in).
 cudaError_t launch_naive_step(int stencil, int dtype, const void* in, void* out, int64_t N,
-                              const Consts& c, cudaStream_t s);
+                              const Consts& c, cudaStream_t s, bool pdl = false);
 
 // Conversion and reductions.
 cudaError_t launch_split(int64_t N, const double* u64, float* u32c, cudaStream_t s);

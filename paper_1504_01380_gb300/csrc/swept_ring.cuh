@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 swept_ring_kernel(const StageArgs a, int nwarps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
+  griddep_wait_and_release();
   E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * 32 * K);
   const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (gw >= nwarps) return;
@@ -236,8 +237,8 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
   }
   if (nwarps > a.nwin) nwarps = a.nwin;
   const int grid = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  swept_ring_kernel<ST, DT, K><<<grid, kWarpsPerBlock * 32, smem, s>>>(a, nwarps);
-  return cudaGetLastError();
+  return launch_kernel(a.pdl != 0, swept_ring_kernel<ST, DT, K>, dim3(grid), dim3(kWarpsPerBlock * 32), smem, s,
+                       a, nwarps);
 }
 
 template <int ST, class DT>

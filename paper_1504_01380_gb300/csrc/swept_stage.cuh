@@ -283,6 +283,7 @@ swept_stage_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
   constexpr int B = 32 * K;
+  griddep_wait_and_release();
   E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * B);
   StageImpl<ST, DT, K>::run(a, sm);
 }
@@ -296,8 +297,8 @@ cudaError_t launch_stage_k(const StageArgs& a, cudaStream_t s) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (a.nwin + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  swept_stage_kernel<ST, DT, K><<<grid, kWarpsPerBlock * 32, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(a.pdl != 0, swept_stage_kernel<ST, DT, K>, dim3(grid), dim3(kWarpsPerBlock * 32), smem, s,
+                       a);
 }
 
 template <int ST, class DT>

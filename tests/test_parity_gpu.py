@@ -292,3 +292,19 @@ def test_max_size_heat_f32c_2p31(cuda_lib):
     plan.destroy()
     del u
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("stencil,dtype", [(HEAT, F64), (KS, F32C)])
+def test_plain_launches_same_bits(cuda_lib, stencil, dtype):
+    """SWEPT_OPT_PDL = 0 (plain kernel boundaries instead of programmatic dependent launches):
+    swept and naive give the oracle's bits."""
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    N, B = 32 * 256, 256
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_PDL, 0)
+    u0 = initial(stencil, N, 43)
+    nsteps = 2 * plan.h + 7
+    want = oracle_run(stencil, dtype, u0, nsteps)
+    assert_same(plan, run_gpu(sw, plan, u0, nsteps), want)
+    assert_same(plan, run_gpu(sw, plan, u0, nsteps, naive=True), want)
