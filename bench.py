@@ -48,7 +48,7 @@ TILE_B = 1024
 HEAT_R = 0.25
 METRIC = "cell-updates/s (N x steps / s), swept vs naive stepper, 1 GB300, at stated error"
 UNIT = "cell-updates/s"
-OPS_PER_UPDATE_F32C_HEAT = 10    # 2 sub, add, fma, TwoSum (6): FP32 add/sub/mul/fma instructions
+OPS_PER_UPDATE_F32C_HEAT = 9     # neighbour difference (shared, 1 per point), sub, fma, TwoSum (6)
 OPS_PER_UPDATE_F64_HEAT = 3
 
 
