@@ -50,6 +50,10 @@ METRIC = "cell-updates/s (N x steps / s), swept vs naive stepper, 1 GB300, at st
 UNIT = "cell-updates/s"
 OPS_PER_UPDATE_F32C_HEAT = 9     # neighbour difference (shared, 1 per point), sub, fma, TwoSum (6)
 OPS_PER_UPDATE_F64_HEAT = 3
+# DRAM bytes (read + write) of one swept_ring_kernel<heat, F32C, K=32> launch at N = 2^24,
+# from one ncu capture (profiles/swept_ring_kernel_heat_f32c_K32_N2p24.md).  Update it
+# whenever that kernel changes.
+RING_K32_TRAFFIC_BYTES = 268.592384e6 + 209.810432e6
 
 
 def workload_config(n_gpus: int):
@@ -360,7 +364,9 @@ def run_gpu(args):
     achieved = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * NSTEPS / (t_dev / args.steps)
     roof = {"bound": "alu", "kernel": "swept_ring_kernel<heat,f32c,K=32>",
             "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops, "traffic": None,
+            "frac": achieved / peak_ops, "traffic": RING_K32_TRAFFIC_BYTES,
+            "traffic_unit": "DRAM bytes per launch (ncu)",
+            "algorithmic_edge_bytes_per_launch": 2 * 16 * N_POINTS,
             "per_launch_ops": per_launch_ops, "avg_launch_ms": avg_launch_s * 1e3,
             "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"}
     cpu = time_oracle() if world == 1 else None
