@@ -130,8 +130,8 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *   SWEPT_OPT_DIAMOND    kernel for full diamond stages:
  *                        SWEPT_DIAMOND_AUTO (default: the ring from 8
  *                        windows up, except that with automatic ring warps
- *                        the per-window kernel runs when the GPU holds a
- *                        warp for every window at once), SWEPT_DIAMOND_WINDOW
+ *                        the per-window kernel runs when there is at most one
+ *                        window per warp scheduler, 4 per SM), SWEPT_DIAMOND_WINDOW
  *                        (one warp per window), SWEPT_DIAMOND_RING (one warp
  *                        streams a run of windows, overlapping the V-fill of
  *                        one with the triangle of the previous).
@@ -144,9 +144,9 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        0 (default): launch the stages directly.
  *   SWEPT_OPT_PDL        1 (default): consecutive kernels of an advance (stages;
  *                        the naive stepper's steps) are programmatic dependent
- *                        launches: the next kernel is scheduled while the
- *                        previous one runs and waits for its results on the
- *                        device, hiding the launch gap; 0: plain launches.
+ *                        launches: the next kernel is prepared while the
+ *                        previous one drains and waits for its results on the
+ *                        device, hiding part of the launch gap; 0: plain launches.
  * Errors: SWEPT_EINVAL for an unknown option or value.
  */
 #define SWEPT_OPT_DIAMOND     0

@@ -32,7 +32,7 @@ template <int ST, class DT>
 __global__ void __launch_bounds__(kNaiveThreads)
 naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N, const Consts c) {
   constexpr int R = Radius<ST>::value;
-  griddep_wait_and_release();
+  griddep_wait();
   using Cc = typename DT::C;
   const int lane = threadIdx.x & 31;
   const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kNaiveThreads)
 naive_rk2_kernel(int sub, const double* __restrict__ u, const double* __restrict__ m,
                  double* __restrict__ out, int64_t N, const Consts c) {
   constexpr int R = Radius<ST>::value;
-  griddep_wait_and_release();
+  griddep_wait();
   const int lane = threadIdx.x & 31;
   const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
   const bool valid = i0 < N;
@@ -143,7 +143,7 @@ naive_euler_kernel(const T* __restrict__ arg, const T* __restrict__ base, const 
                    T* __restrict__ out, T* __restrict__ out_lo, int64_t N, T ca, T g1) {
   using O = EOps<T>;
   __shared__ T sa[3][kEulerT + 3], ss[3][kEulerT + 1], sf[3][kEulerT];
-  griddep_wait_and_release();
+  griddep_wait();
   const int64_t b0 = (int64_t)blockIdx.x * (kEulerT - 1);
   for (int j = threadIdx.x; j < kEulerT + 3; j += kEulerT) {
     int64_t g = (b0 - 2 + j) % N;

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 swept_ring_kernel(const StageArgs a, int nwarps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
-  griddep_wait_and_release();
+  griddep_wait();
   E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * 32 * K);
   const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (gw >= nwarps) return;
@@ -212,10 +212,13 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
 
 // Launch with `nwarps` warps; 0 picks min(resident warp slots of the GPU,
 // nwin / 2), so that every warp streams at least two windows when it can.
-// nwarps < 0 is the automatic choice of kernel: when the GPU holds a warp for
-// every window at once, the per-window kernel (2h levels per warp) finishes
-// the stage sooner than ring runs of n windows (n + 1 slots of h levels), so
-// that kernel is launched instead; otherwise as for 0.
+// nwarps < 0 is the automatic choice of kernel.  With at most one window per
+// scheduler (nwin <= 4 x SMs) every warp runs alone on its scheduler and the
+// stage time is one warp's chain of levels: the per-window kernel (2h levels)
+// finishes sooner than ring runs of two windows (3h levels), so that kernel
+// is launched instead.  With more windows the pipes are shared and total work
+// decides: the ring computes (n+1) h (K+r) slot-levels per n windows against
+// 2h K for the per-window kernel, so the ring runs (as for 0).
 template <int ST, class DT, int K>
 cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
   const size_t smem = ring_smem_bytes<ST, DT, K>();
@@ -230,7 +233,7 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
                                                       kWarpsPerBlock * 32, smem);
     if (e != cudaSuccess) return e;
     const int resident = sms * (per_sm > 0 ? per_sm : 1) * kWarpsPerBlock;
-    if (nwarps < 0 && a.nwin <= resident) return launch_stage_k<ST, DT, K>(a, s);
+    if (nwarps < 0 && a.nwin <= 4 * sms) return launch_stage_k<ST, DT, K>(a, s);
     nwarps = resident;
     if (nwarps > a.nwin / 2) nwarps = a.nwin / 2;
     if (nwarps < 1) nwarps = 1;

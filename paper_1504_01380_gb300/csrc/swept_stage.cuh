@@ -283,7 +283,7 @@ swept_stage_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
   constexpr int B = 32 * K;
-  griddep_wait_and_release();
+  griddep_wait();
   E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * B);
   StageImpl<ST, DT, K>::run(a, sm);
 }
