@@ -136,7 +136,7 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        streams a run of windows, overlapping the V-fill of
  *                        one with the triangle of the previous).
  *   SWEPT_OPT_RING_WARPS warps of a ring launch; 0 = min(resident warp slots,
- *                        N/B/2).
+ *                        N/B/2), and at most 4 per SM for FP64 states.
  *   SWEPT_OPT_GRAPH      1: swept_advance captures its stage sequence into a
  *                        CUDA graph on the first call for a given (u, nsteps)
  *                        and replays it afterwards (fewer host launches: the

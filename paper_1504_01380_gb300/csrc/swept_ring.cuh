@@ -211,7 +211,8 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
 }
 
 // Launch with `nwarps` warps; 0 picks min(resident warp slots of the GPU,
-// nwin / 2), so that every warp streams at least two windows when it can.
+// nwin / 2), so that every warp streams at least two windows when it can,
+// and for FP64 states at most one warp per scheduler (4 per SM).
 // nwarps < 0 is the automatic choice of kernel.  With at most one window per
 // scheduler (nwin <= 4 x SMs) every warp runs alone on its scheduler and the
 // stage time is one warp's chain of levels: the per-window kernel (2h levels)
@@ -219,6 +220,13 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
 // is launched instead.  With more windows the pipes are shared and total work
 // decides: the ring computes (n+1) h (K+r) slot-levels per n windows against
 // 2h K for the per-window kernel, so the ring runs (as for 0).
+// FP64 states run on GB300's narrow FP64 pipe: one warp per scheduler already
+// keeps it busy, and fewer, longer ring runs waste fewer fill and drain slots.
+template <class DT> struct FP64Pipe { static constexpr bool value = false; };
+template <> struct FP64Pipe<F64> { static constexpr bool value = true; };
+template <> struct FP64Pipe<F64P> { static constexpr bool value = true; };
+template <> struct FP64Pipe<F64E> { static constexpr bool value = true; };
+
 template <int ST, class DT, int K>
 cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
   const size_t smem = ring_smem_bytes<ST, DT, K>();
@@ -235,6 +243,7 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
     const int resident = sms * (per_sm > 0 ? per_sm : 1) * kWarpsPerBlock;
     if (nwarps < 0 && a.nwin <= 4 * sms) return launch_stage_k<ST, DT, K>(a, s);
     nwarps = resident;
+    if (FP64Pipe<DT>::value && nwarps > 4 * sms) nwarps = 4 * sms;
     if (nwarps > a.nwin / 2) nwarps = a.nwin / 2;
     if (nwarps < 1) nwarps = 1;
   }
