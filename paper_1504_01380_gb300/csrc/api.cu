@@ -373,6 +373,10 @@ cudaError_t adjoint_sweep(swept_plan_s* p, double* lam, int64_t len, const doubl
     a.eout = buf[k & 1];
     a.lev_fill = k >= 1 ? (k - 1) * H : 0;
     a.lev_trap = k * H;
+    if (use_ring(p) && hv == p->H && ht == p->H) {
+      const int w = (p->diamond == SWEPT_DIAMOND_AUTO && p->ring_warps == 0) ? -1 : p->ring_warps;
+      return swept::launch_ring_ksadj_f64(p->K, a, w, s);
+    }
     return swept::launch_stage_ksadj_f64(p->K, a, s);
   };
   cudaError_t e = cudaSuccess;

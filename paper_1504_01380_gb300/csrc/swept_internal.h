@@ -71,8 +71,9 @@ cudaError_t launch_ring_ks_f32c(int K, const StageArgs& a, int nwarps, cudaStrea
 cudaError_t launch_ring_heat_f32(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 cudaError_t launch_ring_ks_f32(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 
-// Adjoint (transposed KS, FP64) stage over a tape.
+// Adjoint (transposed KS, FP64) stage over a tape; the ring version for full diamonds.
 cudaError_t launch_stage_ksadj_f64(int K, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_ring_ksadj_f64(int K, const StageArgs& a, int nwarps, cudaStream_t s);
 
 // Two-stage Runge-Kutta stencils (FP64, state pairs (u, m) on chip).
 cudaError_t launch_stage_heatrk2_f64(int K, const StageArgs& a, cudaStream_t s);

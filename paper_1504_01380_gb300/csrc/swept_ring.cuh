@@ -112,6 +112,42 @@ struct RingImpl {
     for (int i = lane; i < n16; i += 32) d4[i] = s4[i];
   }
 
+  // Adjoint sweeps: the forward state (the coefficient of the transposed step)
+  // at each of this lane's S ring slots for the level being computed
+  // (mp + 1 of the slot).  Ring position p (relative to the fill window's
+  // start c) is fill-window point p, computed on the V [B/2 - r(mp+1),
+  // B/2 + r(mp+1)), and emptied-window point p - M/2 (mod M), computed on
+  // [r(mp+1), B - r(mp+1)); the two are disjoint at every level.  Slots
+  // outside both get 0 (their values are never read).  Sweep level tau uses
+  // forward level tape_len - tau.
+  static __device__ __forceinline__ void adjoint_coef(double (&cf)[S], const StageArgs& a, int lane, int cl,
+                                                      int wfill, bool fill, bool empty, int mp) {
+    constexpr int M = 32 * S;
+    const int lo_f = B / 2 - R * (mp + 1), hi_f = B / 2 + R * (mp + 1);
+    const int lo_t = R * (mp + 1), hi_t = B - R * (mp + 1);
+    const double* rf = a.tape + (a.tape_len - (a.lev_fill + mp + 1)) * a.N;
+    const double* rt = a.tape + (a.tape_len - (a.lev_trap + mp + 1)) * a.N;
+    const int64_t wsf = (int64_t)wfill * B + a.offset;
+    const int64_t wst = wsf - B;                       // the emptied window is wfill - 1
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      const int p = (((lane - cl) & 31) * S + k) % M;
+      const int xt = (p + M / 2) % M;
+      double v = 0.0;
+      if (fill && p >= lo_f && p < hi_f) {
+        int64_t g = wsf + p;
+        if (g >= a.N) g -= a.N;
+        v = rf[g];
+      } else if (empty && xt >= lo_t && xt < hi_t) {
+        int64_t g = wst + xt;
+        if (g < 0) g += a.N;
+        if (g >= a.N) g -= a.N;
+        v = rt[g];
+      }
+      cf[k] = v;
+    }
+  }
+
   // Hooks of a run without dependences (one launch per stage).
   struct NoHooks {
     __device__ __forceinline__ bool ready(int) const { return true; }
@@ -172,8 +208,14 @@ struct RingImpl {
         // Several sub-timesteps per step: both windows are at the same
         // level modulo Subs (h is a multiple of Subs), so one sub-timestep
         // serves the whole ring
-        tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, nullptr,
-                                     (int)((a.lev_fill + mp) & (Subs<ST>::value - 1)));
+        if constexpr (ST == kKSAdj) {
+          double cf[S];
+          adjoint_coef(cf, a, lane, cl, w0 + slot, fill, empty, mp);
+          tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, cf, 0);
+        } else {
+          tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, nullptr,
+                                       (int)((a.lev_fill + mp) & (Subs<ST>::value - 1)));
+        }
         if (++j == L) { j = 0; ++P; }
       }
       __syncwarp();
@@ -243,7 +285,9 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
     const int resident = sms * (per_sm > 0 ? per_sm : 1) * kWarpsPerBlock;
     if (nwarps < 0 && a.nwin <= 4 * sms) return launch_stage_k<ST, DT, K>(a, s);
     nwarps = resident;
-    if (FP64Pipe<DT>::value && nwarps > 4 * sms) nwarps = 4 * sms;
+    // (the adjoint sweep also waits on its tape loads every level: two warps per scheduler)
+    const int cap = (ST == kKSAdj ? 8 : 4) * sms;
+    if (FP64Pipe<DT>::value && nwarps > cap) nwarps = cap;
     if (nwarps > a.nwin / 2) nwarps = a.nwin / 2;
     if (nwarps < 1) nwarps = 1;
   }

@@ -45,6 +45,22 @@ def test_ks_adjoint_segmentation_invariant(cuda_lib):
     assert np.array_equal(outs[0], oracle.adjoint_f64(1, KS_PRM, u0, lam, nsteps))
 
 
+@pytest.mark.parametrize("B,warps", [(128, 1), (128, 3), (128, 0), (256, 2)])
+def test_ks_adjoint_ring_sweep_matches_oracle(cuda_lib, B, warps):
+    """The transposed sweep on the ring kernel (forced, with several run lengths): each slot
+    reads the forward state of the window and level it computes; bit-exact against the oracle."""
+    sw = cuda_lib
+    n = 32 * B
+    u0 = workloads.ks_smoothed(n, 9) * 10
+    lam = workloads.uniform(n, 10)
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, KS_PRM, sw.SWEPT_F64, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, warps)
+    for nsteps, K in ((4 * plan.h + 3, 1), (7 * plan.h, 2), (5 * plan.h + 11, 64)):
+        got = sw.swept_adjoint(plan, dev(u0), dev(lam), nsteps, K).cpu().numpy()
+        assert np.array_equal(got, oracle.adjoint_f64(1, KS_PRM, u0, lam, nsteps)), (nsteps, K)
+
+
 def test_heat_adjoint_is_forward_2n(cuda_lib):
     """Heat: grad of 1/2 sum u(T)^2 = A^(2n) u0 (A symmetric), bit for bit."""
     sw = cuda_lib
