@@ -373,6 +373,7 @@ def run_gpu(args):
     naive_roof = hbm * 1e9 / 16.0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+            "ms_per_step_median": statistics.median(ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32c",
             "data": "synthetic", "config": workload_config(world),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N_POINTS,
@@ -383,6 +384,7 @@ def run_gpu(args):
             "compare": {"naive_f32c": naive_f32c, "swept_f64": swept_f64, "naive_f64": naive_f64,
                         "swept_f32_plain": swept_f32, "max_err_f32_plain_vs_exact": err_f32,
                         "naive_hbm_roof_16B": naive_roof, "swept_over_naive_hbm_roof": value / world / naive_roof,
+                        "swept_over_naive_f32c": value / world / naive_f32c,
                         "ops_per_update": {"f32c_heat": OPS_PER_UPDATE_F32C_HEAT, "f64_heat": OPS_PER_UPDATE_F64_HEAT},
                         "tile_sweep_f32c": sweep},
             "wall_s": wall}
