@@ -708,6 +708,16 @@ def run_latency_workload(args):
     sw.swept_plan_set(plan, sw.SWEPT_OPT_PDL, 0)
     swept_graph_nopdl = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
     plan.destroy()
+    # every stage in one persistent launch (device flags instead of kernel boundaries)
+    persistent = {}
+    for B in (32, 64, 128):
+        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, B)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_PERSISTENT, 1)
+        persistent[str(B)] = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
+        status = sw.swept_plan_status(plan)
+        plan.destroy()
+        if status != 0:
+            persistent[str(B)] = None
     fit = tune.fit_eq1([(int(b), t) for b, t in swept_graph.items()])
     best = min(swept_graph, key=swept_graph.get)
     line = {"metric": "time per sub-timestep (latency regime)", "value": swept_graph[best] * 1e9,
@@ -718,6 +728,7 @@ def run_latency_workload(args):
             "swept_graph_ns": {b: t * 1e9 for b, t in swept_graph.items()},
             "naive_ns": naive * 1e9, "naive_graph_ns": naive_graph * 1e9,
             "without_pdl": {"swept_graph_ns_B32": swept_graph_nopdl * 1e9, "naive_graph_ns": naive_graph_nopdl * 1e9},
+            "swept_persistent_ns": {b: (t * 1e9 if t is not None else None) for b, t in persistent.items()},
             "speedup_vs_naive": naive / swept_graph[best],
             "speedup_vs_naive_graph": naive_graph / swept_graph[best],
             "eq1_fit": {"s_ns": fit["s"] * 1e9, "tau_ns": fit["tau"] * 1e9,

@@ -147,12 +147,21 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        launches: the next kernel is prepared while the
  *                        previous one drains and waits for its results on the
  *                        device, hiding part of the launch gap; 0: plain launches.
+ *   SWEPT_OPT_PERSISTENT 1: forward-Euler heat and KS advances with K <= 8 whose
+ *                        windows can all be resident at once run every stage
+ *                        in one launch, each warp waiting (bounded, 2 s) on
+ *                        device flags for the two windows it reads from before
+ *                        each stage: no stage boundary at all (the latency
+ *                        regime); other plans ignore it.  0 (default): off.
+ *                        A wait that runs out ends the launch with the status
+ *                        SWEPT_ETIMEOUT, read by swept_plan_status.
  * Errors: SWEPT_EINVAL for an unknown option or value.
  */
 #define SWEPT_OPT_DIAMOND     0
 #define SWEPT_OPT_RING_WARPS  1
 #define SWEPT_OPT_GRAPH       2
 #define SWEPT_OPT_PDL         3
+#define SWEPT_OPT_PERSISTENT  4
 #define SWEPT_DIAMOND_AUTO    0
 #define SWEPT_DIAMOND_WINDOW  1
 #define SWEPT_DIAMOND_RING    2
@@ -186,6 +195,13 @@ int swept_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream);
  * Same arguments and errors as swept_advance.
  */
 int swept_naive_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream);
+
+/*
+ * swept_plan_status -- synchronise `stream` and return the device status of
+ * the plan's last persistent advance: SWEPT_OK or SWEPT_ETIMEOUT (a device
+ * wait ran out; the state is then undefined).  Other advances leave it OK.
+ */
+int swept_plan_status(swept_plan_t plan, void *stream);
 
 /* ---- adjoint ----------------------------------------------------------- */
 

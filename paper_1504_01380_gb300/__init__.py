@@ -21,7 +21,7 @@ SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT = 0, 1, 2
 SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP = 0, -1, -2, -3, -4, -5
 SWEPT_ETOOBIG = -6
 SWEPT_NOALLOC_MAX_N = 1 << 20
-SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS, SWEPT_OPT_GRAPH, SWEPT_OPT_PDL = 0, 1, 2, 3
+SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS, SWEPT_OPT_GRAPH, SWEPT_OPT_PDL, SWEPT_OPT_PERSISTENT = 0, 1, 2, 3, 4
 SWEPT_DIAMOND_AUTO, SWEPT_DIAMOND_WINDOW, SWEPT_DIAMOND_RING = 0, 1, 2
 
 RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2, SWEPT_HEAT_RK2: 1, SWEPT_KS_RK2: 2, SWEPT_EULER: 1}
@@ -33,6 +33,7 @@ EXPORTS = (
     "swept_advance_noalloc", "swept_plan_set",
     "swept_batch_plan", "swept_batch_set", "swept_batch_info", "swept_advance_batch",
     "swept_batch_status", "swept_batch_destroy", "swept_adjoint", "swept_batch_naive_advance",
+    "swept_plan_status",
 )
 
 SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH = 0, 1, 2, 3
@@ -96,6 +97,8 @@ def load(path: str | None = None):
         L.swept_advance_batch.restype = i32
         L.swept_batch_naive_advance.argtypes = [vp, vp, vp]
         L.swept_batch_naive_advance.restype = i32
+        L.swept_plan_status.argtypes = [vp, vp]
+        L.swept_plan_status.restype = i32
         L.swept_batch_status.argtypes = [vp, vp]
         L.swept_batch_status.restype = i32
         L.swept_batch_destroy.argtypes = [vp]
@@ -200,6 +203,11 @@ def swept_advance(plan: Plan, u, nsteps: int, stream=None):
     _check(load().swept_advance(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(nsteps),
                                 _stream(stream)), "swept_advance")
     return u
+
+
+def swept_plan_status(plan: Plan, stream=None) -> int:
+    """Synchronise and return the device status of the last persistent advance (0 or SWEPT_ETIMEOUT)."""
+    return int(load().swept_plan_status(plan.handle, _stream(stream)))
 
 
 def swept_naive_advance(plan: Plan, u, nsteps: int, stream=None):

@@ -10,6 +10,7 @@
 
 #include "swept.h"
 #include "swept_internal.h"
+#include "swept_sync.cuh"
 
 using swept::Consts;
 using swept::StageArgs;
@@ -30,6 +31,9 @@ struct swept_plan_s {
   int subs;               // sub-timesteps (levels) per time step: 1, 2 or 4
   int use_graph;          // replay the stage sequence as a CUDA graph
   int pdl;                // programmatic dependent launch between consecutive kernels
+  int persistent;         // SWEPT_OPT_PERSISTENT: 0 off, 1 when eligible
+  int* flags;             // nwin stage counters of the persistent advance
+  int* status;            // its device status word
   cudaGraphExec_t gexec;  // captured advance (valid for g_u, g_nsteps)
   void* g_u;
   int64_t g_nsteps;
@@ -202,9 +206,15 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->edge_half = (size_t)p->nwin * 2 * B * esize;
   cudaError_t e = cudaMalloc((void**)&p->edges, 2 * p->edge_half);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->red, 2 * swept::kReduceBlocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->flags, (size_t)p->nwin * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->status, 0, sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    if (p->edges) cudaFree(p->edges);
+    cudaFree(p->edges);
+    cudaFree(p->red);
+    cudaFree(p->flags);
+    cudaFree(p->status);
     std::free(p);
     return cuda_status(e);
   }
@@ -219,6 +229,8 @@ void swept_destroy(swept_plan_t p) {
   if (p->edges) cudaFree(p->edges);
   if (p->red) cudaFree(p->red);
   if (p->adj) cudaFree(p->adj);
+  cudaFree(p->flags);
+  cudaFree(p->status);
   std::free(p);
 }
 
@@ -250,6 +262,15 @@ int swept_plan_set(swept_plan_t p, int option, int64_t value) {
     }
     return SWEPT_OK;
   }
+  if (option == SWEPT_OPT_PERSISTENT) {
+    if (value != 0 && value != 1) return SWEPT_EINVAL;
+    p->persistent = (int)value;
+    if (p->g_valid) {
+      cudaGraphExecDestroy(p->gexec);
+      p->g_valid = 0;
+    }
+    return SWEPT_OK;
+  }
   if (option == SWEPT_OPT_PDL) {
     if (value != 0 && value != 1) return SWEPT_EINVAL;
     p->pdl = (int)value;
@@ -266,12 +287,54 @@ int swept_plan_set(swept_plan_t p, int option, int64_t value) {
 
 namespace {
 
+// The persistent advance applies to forward-Euler heat and KS with K <= 8 when
+// every window's warp can be resident at once.
+bool persistent_ok(const swept_plan_s* p, int64_t levels) {
+  if (!p->persistent || p->subs != 1 || p->K > 8) return false;
+  if (p->stencil != SWEPT_HEAT && p->stencil != SWEPT_KS) return false;
+  if (levels / p->H > (int64_t)0x3fffffff) return false;
+  swept::PersistArgs pa{};
+  pa.a.nwin = p->nwin;
+  int fits = 0;
+  const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
+  if (swept::launch_persistent(st, p->dtype, p->K, pa, nullptr, false, true, &fits) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return fits != 0;
+}
+
 // Enqueue the stage sequence of one advance (Section 3's stages, A5's schedule).
 int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
   const int64_t levels = p->subs * nsteps;                // sub-timesteps
   const int64_t H = p->H;
   const int64_t q = levels / H;
   const int rem = (int)(levels % H);
+  if (persistent_ok(p, levels)) {
+    swept::PersistArgs pa{};
+    pa.a.u = u;
+    pa.a.N = p->N;
+    pa.a.nwin = p->nwin;
+    pa.a.c = p->c;
+    pa.edges = p->edges;
+    pa.edge_half = p->edge_half;
+    pa.flags = p->flags;
+    pa.status = p->status;
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    if (khz <= 0) khz = 2000000;
+    pa.budget = (long long)(2.0 * (double)khz * 1000.0);      // 2 s per wait
+    pa.q = (int)q;
+    pa.rem = rem;
+    pa.H = (int)H;
+    pa.nstages = q == 0 ? 2 : (rem ? (int)q + 2 : (int)q + 1);
+    cudaError_t e = cudaMemsetAsync(p->flags, 0, (size_t)p->nwin * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
+    const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
+    if (e == cudaSuccess) e = swept::launch_persistent(st, p->dtype, p->K, pa, s, false, false, nullptr);
+    return cuda_status(e);
+  }
   unsigned char* buf[2] = {p->edges, p->edges + p->edge_half};
   StageArgs a{};
   a.u = u;
@@ -526,6 +589,14 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     e = cudaMemcpyAsync(u, p->edges, bytes, cudaMemcpyDeviceToDevice, s);
   }
   return cuda_status(e);
+}
+
+int swept_plan_status(swept_plan_t p, void* stream) {
+  if (!p) return SWEPT_EINVAL;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SWEPT_ECUDA;
+  int st = 0;
+  if (cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SWEPT_ECUDA;
+  return st;
 }
 
 int swept_f32c_split(int64_t N, const double* u64, void* u32c, void* stream) {

@@ -37,6 +37,7 @@
 #include "swept_internal.h"
 #include "swept_ring.cuh"
 #include "swept_stage.cuh"
+#include "swept_sync.cuh"
 
 namespace swept {
 
@@ -68,24 +69,6 @@ struct BatchArgs {
 
 namespace {
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Bounded wait until *flag >= target (acquire).  False when the budget ran out.
-__device__ __forceinline__ bool wait_ge(const int* flag, int target, long long t0, long long budget) {
-  for (;;) {
-    if (ld_acquire(flag) >= target) return true;
-    if (clock64() - t0 > budget) return false;
-    __nanosleep(256);
-  }
-}
-
 template <class T>
 __device__ __forceinline__ int upper_index(const T* a, int n, T x) {
   // largest i in [0, n) with a[i] <= x (a ascending, a[0] <= x)
@@ -97,20 +80,6 @@ __device__ __forceinline__ int upper_index(const T* a, int n, T x) {
   return lo;
 }
 
-__host__ __device__ __forceinline__ void stage_shape(int s, int q, int rem, int H, int& hv, int& ht) {
-  if (q == 0) {
-    hv = s == 0 ? 0 : rem;
-    ht = s == 0 ? rem : 0;
-  } else if (s == 0) {
-    hv = 0; ht = H;
-  } else if (s < q) {
-    hv = H; ht = H;
-  } else if (s == q) {
-    hv = H; ht = rem;
-  } else {
-    hv = rem; ht = 0;
-  }
-}
 
 // Dependence hooks of one item: wait (bounded) for the two windows of the
 // previous stage a window reads from; publish a window after its edges.

@@ -101,6 +101,21 @@ cudaError_t launch_naive_euler_f32c(int full, const float* arg, const float* hi,
 cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
                              const Consts& c, cudaStream_t s, bool pdl = false);
 
+// Persistent advance (every stage in one launch, windows synchronised by
+// flags): heat and KS, dtype 0 F64 / 1 F32C / 2 F32, K in {1, 2, 4, 8}.
+struct PersistArgs {
+  StageArgs a;                  // u, N, nwin, c (the per-stage fields are set on the device)
+  unsigned char* edges;         // the edge double buffer
+  size_t edge_half;             // bytes per buffer
+  int* flags;                   // nwin counters of completed stages (zero before the launch)
+  int* status;                  // SWEPT_OK, or SWEPT_ETIMEOUT when a wait ran out
+  long long budget;             // clock cycles per wait
+  int q, rem, H, nstages;
+};
+// query = true: *fits = 1 when every block of the launch can be resident at once.
+cudaError_t launch_persistent(int stencil, int dtype, int K, const PersistArgs& p, cudaStream_t s, bool pdl,
+                              bool query, int* fits);
+
 // Shared-memory bytes per block of the stage kernel for tile width B and
 // edge elements of esize bytes (8; 16 for the Runge-Kutta pair; 72 or 48
 // for an Euler point state).
