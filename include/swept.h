@@ -155,6 +155,10 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        regime); other plans ignore it.  0 (default): off.
  *                        A wait that runs out ends the launch with the status
  *                        SWEPT_ETIMEOUT, read by swept_plan_status.
+ *   SWEPT_OPT_TIMEOUT_MS budget of each persistent wait, 1..600000 ms (2000).
+ *   SWEPT_OPT_DROP_WINDOW failure injection for the persistent advance: window
+ *                        `value` never publishes its stages (a lost message),
+ *                        so its neighbours' waits run out; -1 (default) none.
  * Errors: SWEPT_EINVAL for an unknown option or value.
  */
 #define SWEPT_OPT_DIAMOND     0
@@ -162,6 +166,8 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
 #define SWEPT_OPT_GRAPH       2
 #define SWEPT_OPT_PDL         3
 #define SWEPT_OPT_PERSISTENT  4
+#define SWEPT_OPT_DROP_WINDOW 5
+#define SWEPT_OPT_TIMEOUT_MS  6
 #define SWEPT_DIAMOND_AUTO    0
 #define SWEPT_DIAMOND_WINDOW  1
 #define SWEPT_DIAMOND_RING    2

@@ -34,6 +34,8 @@ struct swept_plan_s {
   int persistent;         // SWEPT_OPT_PERSISTENT: 0 off, 1 when eligible
   int* flags;             // nwin stage counters of the persistent advance
   int* status;            // its device status word
+  int drop_w;             // SWEPT_OPT_DROP_WINDOW: a window that never publishes (-1: none)
+  double timeout_s;       // SWEPT_OPT_TIMEOUT_MS / 1000: budget of each persistent wait
   cudaGraphExec_t gexec;  // captured advance (valid for g_u, g_nsteps)
   void* g_u;
   int64_t g_nsteps;
@@ -200,6 +202,8 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->rk2 = rk2 ? 1 : 0;
   p->subs = euler ? 4 : (rk2 ? 2 : 1);
   p->pdl = 1;
+  p->drop_w = -1;
+  p->timeout_s = 2.0;
   cudaGetDevice(&p->device);
   const size_t esize = euler ? (dtype == SWEPT_F64 ? sizeof(swept::EulerE) : sizeof(swept::EulerEF))
                               : (rk2 ? 16 : (dtype == SWEPT_F32 ? 4 : 8));
@@ -271,6 +275,24 @@ int swept_plan_set(swept_plan_t p, int option, int64_t value) {
     }
     return SWEPT_OK;
   }
+  if (option == SWEPT_OPT_DROP_WINDOW) {
+    if (value < -1 || value >= p->nwin) return SWEPT_EINVAL;
+    p->drop_w = (int)value;
+    if (p->g_valid) {
+      cudaGraphExecDestroy(p->gexec);
+      p->g_valid = 0;
+    }
+    return SWEPT_OK;
+  }
+  if (option == SWEPT_OPT_TIMEOUT_MS) {
+    if (value < 1 || value > 600000) return SWEPT_EINVAL;
+    p->timeout_s = (double)value / 1000.0;
+    if (p->g_valid) {
+      cudaGraphExecDestroy(p->gexec);
+      p->g_valid = 0;
+    }
+    return SWEPT_OK;
+  }
   if (option == SWEPT_OPT_PDL) {
     if (value != 0 && value != 1) return SWEPT_EINVAL;
     p->pdl = (int)value;
@@ -324,7 +346,8 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
     if (khz <= 0) khz = 2000000;
-    pa.budget = (long long)(2.0 * (double)khz * 1000.0);      // 2 s per wait
+    pa.budget = (long long)(p->timeout_s * (double)khz * 1000.0);   // per wait
+    pa.drop_w = p->drop_w;
     pa.q = (int)q;
     pa.rem = rem;
     pa.H = (int)H;

@@ -63,7 +63,7 @@ swept_persistent_kernel(const PersistArgs p) {
     StageImpl<ST, DT, K>::run_window(a, sm, w);
     // the warp's edge and state stores, then one fence and the release by lane 0
     __syncwarp();
-    if (lane == 0) {
+    if (lane == 0 && w != p.drop_w) {
       __threadfence();
       st_release(p.flags + w, k + 1);
     }

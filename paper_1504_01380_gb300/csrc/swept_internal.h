@@ -111,6 +111,7 @@ struct PersistArgs {
   int* status;                  // SWEPT_OK, or SWEPT_ETIMEOUT when a wait ran out
   long long budget;             // clock cycles per wait
   int q, rem, H, nstages;
+  int drop_w;                   // window whose publishes are dropped (a lost message; -1: none)
 };
 // query = true: *fits = 1 when every block of the launch can be resident at once.
 cudaError_t launch_persistent(int stencil, int dtype, int K, const PersistArgs& p, cudaStream_t s, bool pdl,

@@ -55,3 +55,23 @@ def test_persistent_not_applicable_takes_stage_path(cuda_lib):
     sw.swept_plan_set(plan, sw.SWEPT_OPT_PERSISTENT, 1)
     u0 = initial(HEAT, N, 9)
     assert_same(plan, run_gpu(sw, plan, u0, 1000), oracle_run(HEAT, F32C, u0, 1000))
+
+
+def test_persistent_lost_message_times_out_and_gpu_stays_usable(cuda_lib):
+    """A window whose publishes are dropped (a lost message): its neighbours' bounded waits run
+    out, the status reads SWEPT_ETIMEOUT, and the next advance on the same context is exact."""
+    import torch
+    sw = cuda_lib
+    N, B = 16 * 64, 64
+    plan = sw.swept_plan(N, 1, HEAT, [0.25], F64, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_PERSISTENT, 1)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_TIMEOUT_MS, 200)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DROP_WINDOW, 5)
+    u0 = initial(HEAT, N, 11)
+    run_gpu(sw, plan, u0, 10 * plan.h + 3)
+    assert sw.swept_plan_status(plan) == sw.SWEPT_ETIMEOUT
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DROP_WINDOW, -1)
+    got = run_gpu(sw, plan, u0, 10 * plan.h + 3)
+    assert sw.swept_plan_status(plan) == 0
+    assert_same(plan, got, oracle_run(HEAT, F64, u0, 10 * plan.h + 3))
+    del torch
