@@ -35,6 +35,7 @@ struct swept_plan_s {
   int* flags;             // nwin stage counters of the persistent advance
   int* status;            // its device status word
   int drop_w;             // SWEPT_OPT_DROP_WINDOW: a window that never publishes (-1: none)
+  int nreg;               // uneven tiles: windows [0, nreg) are B wide, the rest B + 32r (nreg = nwin: even)
   double timeout_s;       // SWEPT_OPT_TIMEOUT_MS / 1000: budget of each persistent wait
   cudaGraphExec_t gexec;  // captured advance (valid for g_u, g_nsteps)
   void* g_u;
@@ -132,13 +133,28 @@ bool use_ring(const swept_plan_s* p) {
   return p->nwin >= 8;
 }
 
-// Default tile width: the largest of 512, 256, ... that divides N and keeps
-// K a multiple of the radius (Euler equations: from 64 in FP64, 128 in F32C).
+// Default tile width: the largest of 512, 256, ... that keeps K a multiple
+// of the radius and divides N, or else tiles it with uneven tiles (Euler
+// equations: from 64 in FP64, 128 in F32C).
+// Uneven tiles: N = nreg*B + nwide*(B + 32r) with nwide = (N mod B) / (32r)
+// and nreg >= 0, for the forward-Euler heat and KS stencils in the three
+// single-step precisions with K <= 16.  Returns nreg, or -1 when N cannot be
+// tiled so.
+int64_t uneven_nreg(int64_t N, int B, int radius, int stencil, int dtype) {
+  if (stencil != SWEPT_HEAT && stencil != SWEPT_KS) return -1;
+  if (dtype != SWEPT_F64 && dtype != SWEPT_F32C && dtype != SWEPT_F32) return -1;
+  if (B / 32 > 16 || N % (32 * radius)) return -1;
+  const int64_t extra = N % B;
+  const int64_t nwide = extra / (32 * radius);
+  const int64_t nreg = N / B - nwide;
+  return nreg >= 0 && nreg + nwide >= 1 ? nreg : -1;
+}
+
 int default_B(int64_t N, int radius, int stencil, int dtype) {
   const int kmax = stencil != SWEPT_EULER ? 16 : (dtype == SWEPT_F64 ? 2 : 4);
-  for (int K = kmax; K >= 1; K /= 2) {
+  for (int K = kmax; K >= 1; K /= 2) {           // the widest tile that divides N or tiles it unevenly
     const int B = 32 * K;
-    if (K % radius == 0 && N % B == 0) return B;
+    if (K % radius == 0 && (N % B == 0 || uneven_nreg(N, B, radius, stencil, dtype) >= 0)) return B;
   }
   return 0;
 }
@@ -181,7 +197,11 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32) return SWEPT_ENOTSUP;
   if (euler && K > (dtype == SWEPT_F64 ? 4 : 8)) return SWEPT_ENOTSUP;
   if (K % rad) return SWEPT_EINVAL;
-  if (N % B) return SWEPT_EINVAL;
+  int64_t nreg = N / B;
+  if (N % B) {
+    nreg = uneven_nreg(N, B, rad, stencil_id, dtype);
+    if (nreg < 0) return SWEPT_EINVAL;
+  }
   if (N / B > (int64_t)0x7fffffff) return SWEPT_EINVAL;
   Consts c;
   int st = make_consts(stencil_id, params, nparams, c);
@@ -196,7 +216,8 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->B = B;
   p->K = K;
   p->H = B / (2 * rad);
-  p->nwin = (int)(N / B);
+  p->nwin = (int)(nreg + (N - nreg * B) / (B + 32 * rad));
+  p->nreg = (int)nreg;
   for (int i = 0; i < 3; ++i) p->prm[i] = i < nparams ? params[i] : 0.0;
   p->c = c;
   p->rk2 = rk2 ? 1 : 0;
@@ -312,7 +333,7 @@ namespace {
 // The persistent advance applies to forward-Euler heat and KS with K <= 8 when
 // every window's warp can be resident at once.
 bool persistent_ok(const swept_plan_s* p, int64_t levels) {
-  if (!p->persistent || p->subs != 1 || p->K > 8) return false;
+  if (!p->persistent || p->subs != 1 || p->K > 8 || p->nreg != p->nwin) return false;
   if (p->stencil != SWEPT_HEAT && p->stencil != SWEPT_KS) return false;
   if (levels / p->H > (int64_t)0x3fffffff) return false;
   swept::PersistArgs pa{};
@@ -367,7 +388,8 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
   a.pdl = p->pdl;
   // stage k: windows shifted by B/2 when k is odd (the alternating point
   // sets of Section 3); reads the edges of stage k-1, writes its own.
-  const bool ring = use_ring(p);
+  const bool uneven = p->nreg != p->nwin;
+  const bool ring = use_ring(p) && !uneven;
   auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
     a.offset = (k & 1) ? p->B / 2 : 0;
     a.hv = hv;
@@ -377,7 +399,20 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
     a.lev_fill = k >= 1 ? (k - 1) * H : 0;      // absolute levels (Runge-Kutta parity)
     a.lev_trap = k * H;
     if (ring && hv == p->H && ht == p->H) return launch_ring(p, a, s);
-    return launch_stage(p, a, s);
+    if (!uneven) return launch_stage(p, a, s);
+    // uneven tiles: the B-wide windows, then the wide ones
+    cudaError_t e = cudaSuccess;
+    if (p->nreg > 0) {
+      a.nlaunch = p->nreg;
+      e = launch_stage(p, a, s);
+      a.nlaunch = 0;
+    }
+    if (e != cudaSuccess) return e;
+    const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
+    const int odd = (int)(k & 1);
+    if (p->dtype == SWEPT_F64) return swept::launch_wide_f64(st, p->K, a, p->nreg, odd, s);
+    if (p->dtype == SWEPT_F32C) return swept::launch_wide_f32c(st, p->K, a, p->nreg, odd, s);
+    return swept::launch_wide_f32(st, p->K, a, p->nreg, odd, s);
   };
   cudaError_t e = cudaSuccess;
   if (q == 0) {
@@ -486,7 +521,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
                   int K_cycles, void* stream) {
   if (!p || !u0 || !lam_T || !grad || nsteps < 0) return SWEPT_EINVAL;
   if (!aligned16(u0) || !aligned16(lam_T) || !aligned16(grad)) return SWEPT_EINVAL;
-  if (p->dtype != SWEPT_F64 || p->subs > 1) return SWEPT_ENOTSUP;
+  if (p->dtype != SWEPT_F64 || p->subs > 1 || p->nreg != p->nwin) return SWEPT_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)p->N * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(grad, lam_T, bytes, cudaMemcpyDeviceToDevice, s);

@@ -100,7 +100,7 @@ extern "C" int swept_advance_noalloc(int64_t N, int stencil_id, const double* pa
                            static_cast<unsigned char*>(scratch) + half};
 
   cudaStream_t s = (cudaStream_t)stream;
-  StageArgs a;
+  StageArgs a{};
   a.u = u;
   a.N = N;
   a.nwin = nwin;

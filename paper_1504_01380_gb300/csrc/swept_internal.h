@@ -12,24 +12,26 @@ namespace swept {
 constexpr int kWarpsPerBlock = 4;
 
 // Arguments of one swept stage launch (one window per warp).
+// Every field has a default, so a declared StageArgs is fully defined.
 struct StageArgs {
-  void* u;             // flat state (F64 double[N]; F32C float hi[N], lo[N]; F32 float[N])
-  const void* ein;     // leading edges of the previous stage: nwin * 2B elements
-  void* eout;          // leading edges written by this stage
-  int64_t N;
-  int nwin;            // N / B windows
-  int offset;          // 0: windows [wB, wB+B); B/2: windows shifted right by B/2
-  int hv;              // V-fill height (0 = load the flat state instead)
-  int ht;              // trapezoid height (0 = none; h = full triangle)
-  Consts c;
+  void* u = nullptr;           // flat state (F64 double[N]; F32C float hi[N], lo[N]; F32 float[N])
+  const void* ein = nullptr;   // leading edges of the previous stage: nwin * 2B elements
+  void* eout = nullptr;        // leading edges written by this stage
+  int64_t N = 0;
+  int nwin = 0;                // windows (N / B, or the regular plus the wide ones)
+  int offset = 0;              // 0: windows [wB, wB+B); B/2: windows shifted right by B/2
+  int hv = 0;                  // V-fill height (0 = load the flat state instead)
+  int ht = 0;                  // trapezoid height (0 = none; h = full triangle)
+  Consts c{};
   // Adjoint sweeps only: the forward trajectory of the segment, level n at
   // tape + n*N (FP64), tape_len levels; the sweep's level tau uses the
   // forward level tape_len - tau.  lev_fill / lev_trap: sweep level of the
   // V-fill's base and of the trapezoid's flat base.
-  const double* tape;
-  int64_t tape_len;
-  int64_t lev_fill, lev_trap;
-  int pdl;             // launch with programmatic dependent launch (host side only)
+  const double* tape = nullptr;
+  int64_t tape_len = 0;
+  int64_t lev_fill = 0, lev_trap = 0;
+  int pdl = 0;                 // launch with programmatic dependent launch (host side only)
+  int nlaunch = 0;             // windows launched (0: nwin); uneven tiles launch the regular ones only
 };
 
 // Launch `kern` on `s`; with pdl, as a programmatic dependent launch (the
@@ -100,6 +102,14 @@ cudaError_t launch_naive_euler_f32c(int full, const float* arg, const float* hi,
 // Naive Runge-Kutta sub-timestep: sub 0: m = A(u); sub 1: out = B(u, m).
 cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
                              const Consts& c, cudaStream_t s, bool pdl = false);
+
+// Uneven tiles (N not a multiple of B): the last nwin - nreg windows are
+// B + 32r wide.  One warp per wide window does its V (a regular B window
+// centred on the previous stage's boundary, stored flat to u) and then its
+// trapezoid of the full width from u.  K in {1, 2, 4, 8, 16} (multiple of r).
+cudaError_t launch_wide_f64(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
+cudaError_t launch_wide_f32c(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
+cudaError_t launch_wide_f32(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 
 // Persistent advance (every stage in one launch, windows synchronised by
 // flags): heat and KS, dtype 0 F64 / 1 F32C / 2 F32, K in {1, 2, 4, 8}.

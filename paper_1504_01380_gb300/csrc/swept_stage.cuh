@@ -208,15 +208,27 @@ struct StageImpl {
 
   static __device__ void run(const StageArgs& a, E* sm) {
     const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= a.nwin) return;                     // warp-uniform
+    if (w >= (a.nlaunch ? a.nlaunch : a.nwin)) return;     // warp-uniform
     run_window(a, sm, w);
   }
 
   // The stage on window w (called by one whole warp).
   static __device__ void run_window(const StageArgs& a, E* sm, int w) {
+    const int nw = a.nwin;
+    const int wl = a.offset ? w : (w == 0 ? nw - 1 : w - 1);
+    const int wr = a.offset ? (w + 1 == nw ? 0 : w + 1) : w;
+    run_window_at(a, sm, (int64_t)w * B + a.offset, wl, wr, w, B, false);
+  }
+
+  // The stage on the window of B points starting at ws (< N): V arms from the
+  // right edges of window wl and the left edges of window wr, edges out to
+  // window wo's slot; edge slots of 2*eslot elements.  wrap_points: the
+  // periodic wrap may fall inside a lane's K points (uneven tiles), so the
+  // flat state is loaded point by point.
+  static __device__ void run_window_at(const StageArgs& a, E* sm, int64_t ws, int wl, int wr, int wo, int eslot,
+                                       bool wrap_points) {
     const int lane = threadIdx.x & 31;
     const int64_t N = a.N;
-    const int64_t ws = (int64_t)w * B + a.offset;  // window start, < N
     E* sL = sm;
     E* sR = sm + B;
     Tile<DT, K> t;
@@ -224,13 +236,22 @@ struct StageImpl {
     if (a.hv == 0) {
       int64_t g = ws + (int64_t)lane * K;
       if (g >= N) g -= N;                        // wrap falls on a lane boundary
-      load_points<K>(t, a.u, N, g);
+      if (!wrap_points || g + K <= N) {
+        load_points<K>(t, a.u, N, g);
+      } else {
+        Tile<DT, 1> one;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          int64_t gk = g + k;
+          if (gk >= N) gk -= N;
+          load_points<1>(one, a.u, N, gk);
+          t.put(k, one.get(0));
+        }
+      }
     } else {
-      const int wl = a.offset ? w : (w == 0 ? a.nwin - 1 : w - 1);
-      const int wr = a.offset ? (w + 1 == a.nwin ? 0 : w + 1) : w;
       const E* ein = static_cast<const E*>(a.ein);
-      warp_copy(sL, ein + (int64_t)wl * (2 * B) + B, a.hv * 2 * R, lane);
-      warp_copy(sR, ein + (int64_t)wr * (2 * B), a.hv * 2 * R, lane);
+      warp_copy(sL, ein + (int64_t)wl * (2 * eslot) + eslot, a.hv * 2 * R, lane);
+      warp_copy(sR, ein + (int64_t)wr * (2 * eslot), a.hv * 2 * R, lane);
       __syncwarp();
       vfill(t, sL, sR, a.hv, lane, a, ws);
       __syncwarp();
@@ -238,9 +259,9 @@ struct StageImpl {
     if (a.ht > 0) {
       trapezoid(t, sL, sR, a.ht, lane, a, ws);
       __syncwarp();
-      E* eout = static_cast<E*>(a.eout) + (int64_t)w * (2 * B);
+      E* eout = static_cast<E*>(a.eout) + (int64_t)wo * (2 * eslot);
       warp_copy(eout, sL, a.ht * 2 * R, lane);
-      warp_copy(eout + B, sR, a.ht * 2 * R, lane);
+      warp_copy(eout + eslot, sR, a.ht * 2 * R, lane);
       if (a.ht < H) {
         // top of the trapezoid: level ht on [r ht, B - r ht)
         Coef cf;
@@ -296,7 +317,7 @@ cudaError_t launch_stage_k(const StageArgs& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(swept_stage_kernel<ST, DT, K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = (a.nwin + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int grid = ((a.nlaunch ? a.nlaunch : a.nwin) + kWarpsPerBlock - 1) / kWarpsPerBlock;
   return launch_kernel(a.pdl != 0, swept_stage_kernel<ST, DT, K>, dim3(grid), dim3(kWarpsPerBlock * 32), smem, s,
                        a);
 }
