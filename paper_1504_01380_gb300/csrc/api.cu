@@ -389,7 +389,7 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
   // stage k: windows shifted by B/2 when k is odd (the alternating point
   // sets of Section 3); reads the edges of stage k-1, writes its own.
   const bool uneven = p->nreg != p->nwin;
-  const bool ring = use_ring(p) && !uneven;
+  const bool ring = use_ring(p) && p->nreg > 0;
   auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
     a.offset = (k & 1) ? p->B / 2 : 0;
     a.hv = hv;
@@ -398,13 +398,15 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
     a.eout = buf[k & 1];
     a.lev_fill = k >= 1 ? (k - 1) * H : 0;      // absolute levels (Runge-Kutta parity)
     a.lev_trap = k * H;
-    if (ring && hv == p->H && ht == p->H) return launch_ring(p, a, s);
-    if (!uneven) return launch_stage(p, a, s);
-    // uneven tiles: the B-wide windows, then the wide ones
+    if (!uneven) {
+      if (ring && hv == p->H && ht == p->H) return launch_ring(p, a, s);
+      return launch_stage(p, a, s);
+    }
+    // uneven tiles: the B-wide windows (ring or per window), then the wide ones
     cudaError_t e = cudaSuccess;
     if (p->nreg > 0) {
       a.nlaunch = p->nreg;
-      e = launch_stage(p, a, s);
+      e = (ring && hv == p->H && ht == p->H) ? launch_ring(p, a, s) : launch_stage(p, a, s);
       a.nlaunch = 0;
     }
     if (e != cudaSuccess) return e;

@@ -247,8 +247,9 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
   const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   if (gw >= nwarps) return;
   // balanced contiguous runs: warp gw takes [gw*n/W, (gw+1)*n/W)
-  const int w0 = (int)(((int64_t)gw * a.nwin) / nwarps);
-  const int w1 = (int)(((int64_t)(gw + 1) * a.nwin) / nwarps);
+  const int nw = a.nlaunch ? a.nlaunch : a.nwin;    // windows run (uneven tiles: the regular ones)
+  const int w0 = (int)(((int64_t)gw * nw) / nwarps);
+  const int w1 = (int)(((int64_t)(gw + 1) * nw) / nwarps);
   if (w1 > w0) RingImpl<ST, DT, K>::run(a, sm, w0, w1);
 }
 
@@ -272,6 +273,7 @@ template <> struct FP64Pipe<F64E> { static constexpr bool value = true; };
 template <int ST, class DT, int K>
 cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
   const size_t smem = ring_smem_bytes<ST, DT, K>();
+  const int nw = a.nlaunch ? a.nlaunch : a.nwin;     // windows run
   cudaError_t e = cudaFuncSetAttribute(swept_ring_kernel<ST, DT, K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -283,15 +285,15 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
                                                       kWarpsPerBlock * 32, smem);
     if (e != cudaSuccess) return e;
     const int resident = sms * (per_sm > 0 ? per_sm : 1) * kWarpsPerBlock;
-    if (nwarps < 0 && a.nwin <= 4 * sms) return launch_stage_k<ST, DT, K>(a, s);
+    if (nwarps < 0 && nw <= 4 * sms) return launch_stage_k<ST, DT, K>(a, s);
     nwarps = resident;
     // (the adjoint sweep also waits on its tape loads every level: two warps per scheduler)
     const int cap = (ST == kKSAdj ? 8 : 4) * sms;
     if (FP64Pipe<DT>::value && nwarps > cap) nwarps = cap;
-    if (nwarps > a.nwin / 2) nwarps = a.nwin / 2;
+    if (nwarps > nw / 2) nwarps = nw / 2;
     if (nwarps < 1) nwarps = 1;
   }
-  if (nwarps > a.nwin) nwarps = a.nwin;
+  if (nwarps > nw) nwarps = nw;
   const int grid = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
   return launch_kernel(a.pdl != 0, swept_ring_kernel<ST, DT, K>, dim3(grid), dim3(kWarpsPerBlock * 32), smem, s,
                        a, nwarps);

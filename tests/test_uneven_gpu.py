@@ -56,3 +56,20 @@ def test_uneven_adjoint_not_supported(cuda_lib):
     with pytest.raises(sw.SweptError) as e:
         sw.swept_adjoint(plan, z, z, 5)
     assert e.value.code == sw.SWEPT_ENOTSUP
+
+
+@pytest.mark.parametrize("stencil,dtype,B,warps", [(HEAT, F32C, 128, 3), (HEAT, F64, 64, 0), (KS, F32C, 256, 2),
+                                                   (KS, F64, 128, 0)])
+def test_uneven_with_ring_for_the_regular_windows(cuda_lib, stencil, dtype, B, warps):
+    """The regular windows' full diamonds on the ring kernel (forced; several run lengths), the
+    wide windows alongside."""
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    nwide = max(1, (B // (32 * r)) - 1)
+    N = 20 * B + nwide * (B + 32 * r)
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, warps)
+    u0 = initial(stencil, N, 4000 + B)
+    for nsteps in (4 * plan.h + 3, 6 * plan.h):
+        assert_same(plan, run_gpu(sw, plan, u0, nsteps), oracle_run(stencil, dtype, u0, nsteps))
