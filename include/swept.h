@@ -102,12 +102,12 @@ typedef struct swept_plan_s *swept_plan_t;
  * Defines the problem of Section 3: a periodic 1D grid of N points split
  * into N/B tiles of B points, each advanced by the stencil `stencil_id`
  * (radius `radius`, parameters `params[0..nparams)`) in arithmetic `dtype`.
- *   N       >= B, N % B == 0; or, for the forward-Euler heat and KS stencils
- *           in F64, F32C and F32 with K <= 16, any N that is a multiple of
- *           32*radius and at least (N mod B)/(32 radius) tiles long: the
- *           last (N mod B)/(32 radius) windows are then B + 32 radius wide
- *           (uneven tiles: their trapezoids keep the height h, their Vs stay
- *           B wide).  swept_adjoint does not take uneven plans.
+ *   N       >= B, N % B == 0; or (K <= 16; Euler equations K <= 4 in FP64,
+ *           8 compensated) any N that is a multiple of 32*radius and at
+ *           least (N mod B)/(32 radius) tiles long: the last (N mod B)/(32
+ *           radius) windows are then B + 32 radius wide (uneven tiles: their
+ *           trapezoids keep the height h, their Vs stay B wide).
+ *           swept_adjoint does not take uneven plans.
  *   radius  must equal the stencil's radius (1 heat, 2 KS, either time
  *           integrator; 1 Euler equations).
  *   B       tile width: 32*K points with K in {1,2,4,8,16,32}, K % radius

@@ -137,13 +137,16 @@ bool use_ring(const swept_plan_s* p) {
 // of the radius and divides N, or else tiles it with uneven tiles (Euler
 // equations: from 64 in FP64, 128 in F32C).
 // Uneven tiles: N = nreg*B + nwide*(B + 32r) with nwide = (N mod B) / (32r)
-// and nreg >= 0, for the forward-Euler heat and KS stencils in the three
-// single-step precisions with K <= 16.  Returns nreg, or -1 when N cannot be
-// tiled so.
+// and nreg >= 0, for every stencil and precision the plan takes with K <= 16
+// (Euler equations: K <= 4 in FP64, 8 compensated).  Returns nreg, or -1
+// when N cannot be tiled so.
 int64_t uneven_nreg(int64_t N, int B, int radius, int stencil, int dtype) {
-  if (stencil != SWEPT_HEAT && stencil != SWEPT_KS) return -1;
-  if (dtype != SWEPT_F64 && dtype != SWEPT_F32C && dtype != SWEPT_F32) return -1;
-  if (B / 32 > 16 || N % (32 * radius)) return -1;
+  if (stencil == SWEPT_EULER) {
+    if (B / 32 > (dtype == SWEPT_F64 ? 4 : 8)) return -1;
+  } else if (B / 32 > 16) {
+    return -1;
+  }
+  if (N % (32 * radius)) return -1;
   const int64_t extra = N % B;
   const int64_t nwide = extra / (32 * radius);
   const int64_t nreg = N / B - nwide;
@@ -410,8 +413,12 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
       a.nlaunch = 0;
     }
     if (e != cudaSuccess) return e;
-    const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
     const int odd = (int)(k & 1);
+    if (p->stencil == SWEPT_EULER) return swept::launch_wide_euler(p->dtype, p->K, a, p->nreg, odd, s);
+    if (p->stencil == SWEPT_HEAT_RK2)
+      return swept::launch_wide_rk2(swept::kHeatRK2, p->K, a, p->nreg, odd, s);
+    if (p->stencil == SWEPT_KS_RK2) return swept::launch_wide_rk2(swept::kKSRK2, p->K, a, p->nreg, odd, s);
+    const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
     if (p->dtype == SWEPT_F64) return swept::launch_wide_f64(st, p->K, a, p->nreg, odd, s);
     if (p->dtype == SWEPT_F32C) return swept::launch_wide_f32c(st, p->K, a, p->nreg, odd, s);
     return swept::launch_wide_f32(st, p->K, a, p->nreg, odd, s);

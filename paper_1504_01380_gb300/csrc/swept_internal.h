@@ -106,10 +106,13 @@ cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double
 // Uneven tiles (N not a multiple of B): the last nwin - nreg windows are
 // B + 32r wide.  One warp per wide window does its V (a regular B window
 // centred on the previous stage's boundary, stored flat to u) and then its
-// trapezoid of the full width from u.  K in {1, 2, 4, 8, 16} (multiple of r).
+// trapezoid of the full width from u.  K in {1, 2, 4, 8, 16} (multiple of r;
+// Euler equations: K <= 4 in FP64, K <= 8 compensated).
 cudaError_t launch_wide_f64(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 cudaError_t launch_wide_f32c(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 cudaError_t launch_wide_f32(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
+cudaError_t launch_wide_rk2(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
+cudaError_t launch_wide_euler(int dtype, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 
 // Persistent advance (every stage in one launch, windows synchronised by
 // flags): heat and KS, dtype 0 F64 / 1 F32C / 2 F32, K in {1, 2, 4, 8}.

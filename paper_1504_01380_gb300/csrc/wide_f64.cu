@@ -1,66 +1,8 @@
-// Uneven tiles, F64 state (N not a multiple of the tile width B): the swept stages with
-// the last windows B + 32r wide.  Every V between two tiles stays exactly B
-// wide (Section 3's V grows by r points per side per level around a tile
-// boundary, whatever the tiles' widths), so a wide window of width W = B +
-// 32r is its V (a regular B window centred on the previous stage's boundary)
-// plus the flat top of the wide trapezoid of the previous stage, W - B points
-// already at the stage's base level.  Windows keep their indices from stage
-// to stage; their parts alternate sides: at odd stages the window starts B/2
-// to the right and its V is at its right end, at even stages its V is at its
-// left end.  One warp per wide window: the V part (regular per-window code)
-// stores its flat level to the state, then the trapezoid of the full width
-// W (per-window code of K + r points per lane) reloads it with the top part
-// from the state, writes its edges to the window's slot and stores its own
-// flat top for the next stage.
-#include "swept_stage.cuh"
+// Wide windows of uneven tiles: forward-Euler heat and KS, F64 state.
+#include "swept_wide.cuh"
 
 namespace swept {
-
 namespace {
-
-template <int ST, class DT, int K, int KW>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-swept_wide_kernel(const StageArgs a, int nreg, int odd) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  using E = typename DT::E;
-  constexpr int B = 32 * K, BW = 32 * KW;
-  griddep_wait();
-  E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * BW);
-  const int i = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int j = nreg + i;
-  if (j >= a.nwin) return;                                   // warp-uniform
-  const int64_t N = a.N;
-  const int64_t xj = (int64_t)j * B + (int64_t)i * (BW - B);   // start of tile j at stage 0
-  const int64_t xj1 = j + 1 == a.nwin ? N : xj + BW;
-  if (a.hv > 0) {
-    StageArgs av = a;
-    av.ht = 0;
-    const int64_t vs = odd ? xj1 - B / 2 : xj;
-    const int wl = odd ? j : (j == 0 ? a.nwin - 1 : j - 1);
-    const int wr = odd ? (j + 1 == a.nwin ? 0 : j + 1) : j;
-    StageImpl<ST, DT, K>::run_window_at(av, sm, vs, wl, wr, j, B, false);
-    __syncwarp();
-  }
-  if (a.ht > 0) {
-    StageArgs at = a;
-    at.hv = 0;
-    const int64_t ws = odd ? xj + B / 2 : xj;
-    StageImpl<ST, DT, KW>::run_window_at(at, sm, ws, 0, 0, j, B, true);
-  }
-}
-
-template <int ST, class DT, int K, int KW>
-cudaError_t launch_wk(const StageArgs& a, int nreg, int odd, cudaStream_t s) {
-  const size_t smem = stage_smem_bytes(32 * KW, (int)sizeof(typename DT::E));
-  cudaError_t e = cudaFuncSetAttribute(swept_wide_kernel<ST, DT, K, KW>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int nwide = a.nwin - nreg;
-  const int grid = (nwide + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  return launch_kernel(a.pdl != 0, swept_wide_kernel<ST, DT, K, KW>, dim3(grid), dim3(kWarpsPerBlock * 32), smem,
-                       s, a, nreg, odd);
-}
-
 template <class DT>
 cudaError_t launch_wide_dt(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s) {
   if (stencil == kHeat) {
@@ -81,11 +23,9 @@ cudaError_t launch_wide_dt(int stencil, int K, const StageArgs& a, int nreg, int
     default: return cudaErrorInvalidValue;
   }
 }
-
 }  // namespace
 
 cudaError_t launch_wide_f64(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s) {
   return launch_wide_dt<F64>(stencil, K, a, nreg, odd, s);
 }
-
 }  // namespace swept

@@ -1,9 +1,10 @@
 """Uneven tiles (N not a multiple of the tile width): the last windows are B + 32r wide.  Swept
-advances bit-exact against the oracle for both stencils, the three single-step precisions,
-several tile widths and mixes of regular and wide windows (none regular, one wide, several
-wide), for step counts around every stage boundary."""
+advances bit-exact against the oracle for heat and KS in the three single-step precisions, the
+Runge-Kutta stencils and the Euler equations, several tile widths and mixes of regular and wide
+windows (none regular, one wide, several wide), for step counts around every stage boundary."""
 from __future__ import annotations
 
+import numpy as np
 import pytest
 
 from tests.test_parity_gpu import HEAT, KS, F64, F32C, F32, params_of, initial, oracle_run, run_gpu, assert_same
@@ -73,3 +74,33 @@ def test_uneven_with_ring_for_the_regular_windows(cuda_lib, stencil, dtype, B, w
     u0 = initial(stencil, N, 4000 + B)
     for nsteps in (4 * plan.h + 3, 6 * plan.h):
         assert_same(plan, run_gpu(sw, plan, u0, nsteps), oracle_run(stencil, dtype, u0, nsteps))
+
+
+@pytest.mark.parametrize("st,B,nreg,nwide", [(2, 64, 3, 1), (2, 128, 5, 3), (3, 128, 2, 1), (3, 256, 4, 3)])
+def test_uneven_runge_kutta(cuda_lib, st, B, nreg, nwide):
+    """Two-stage Runge-Kutta (heat 2, KS 3) on uneven tiles: bit-exact against the RK2 oracle."""
+    from tests.test_rk2_gpu import prm, initial as rk2_initial, run as rk2_run
+    import oracle
+    sw = cuda_lib
+    r = 1 if st == 2 else 2
+    N = nreg * B + nwide * (B + 32 * r)
+    plan = sw.swept_plan(N, r, st, prm(st), F64, B)
+    u0 = rk2_initial(st, N, 5000 + B)
+    steps_per_stage = plan.h // 2
+    for nsteps in (1, steps_per_stage, 3 * steps_per_stage + 2):
+        got = rk2_run(sw, plan, u0, nsteps)
+        assert np.array_equal(got, oracle.advance_rk2_f64(st, prm(st), u0, nsteps)), nsteps
+
+
+@pytest.mark.parametrize("dtype,B,nreg,nwide", [(F64, 64, 3, 1), (F64, 128, 2, 2), (F32C, 128, 4, 3),
+                                                (F32C, 256, 1, 5)])
+def test_uneven_euler(cuda_lib, dtype, B, nreg, nwide):
+    """Euler equations on uneven tiles: bit-exact against the Euler oracles."""
+    from tests.test_euler_gpu import state, run as euler_run, oracle_run as euler_oracle, assert_same as euler_same
+    sw = cuda_lib
+    N = nreg * B + nwide * (B + 32)
+    q, prm_e = state(N, 6000 + B)
+    plan = sw.swept_plan(N, 1, 4, prm_e, dtype, B)
+    per_stage = plan.h // 4
+    for nsteps in (1, per_stage, 3 * per_stage + 1):
+        euler_same(euler_run(sw, plan, q, nsteps), euler_oracle(prm_e, q, nsteps, dtype))
