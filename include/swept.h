@@ -111,7 +111,7 @@ typedef struct swept_plan_s *swept_plan_t;
  *   radius  must equal the stencil's radius (1 heat, 2 KS, either time
  *           integrator; 1 Euler equations).
  *   B       tile width: 32*K points with K in {1,2,4,8,16,32}, K % radius
- *           == 0 (Section 3 asks for an even number of points per node; in
+ *           == 0 (Section 3 gives each node an even count of points; in
  *           general B % (2*radius) == 0).  B = 0 picks the tuned default.
  *   params  host pointer; copied.
  * Allocates the edge double-buffer (2 * 2N values, 32N bytes; 64N for the
