@@ -68,29 +68,42 @@ struct RingImpl {
     static constexpr int XGR = 16 * S - 16 * R + R * J + Q;
   };
 
+  // Lane tests.  A position X (relative to the filled window's start) moving
+  // +P lanes per phase is in lane (cl + X/S + P) mod 32, i.e. in the lane
+  // whose (lane - cl - P) mod 32 is (X/S) mod 32; one moving -P lanes, in the
+  // lane whose (lane - cl + P) mod 32 is.  The run keeps those two residues
+  // per phase, set to -1 (no lane) in slots that do not capture (first slot)
+  // or do not place (last slot), so each test is one compare with a constant.
+  struct Lanes {
+    int cap_p, cap_m;   // captures: shrink-left edge (+P), shrink-right edge (-P)
+    int put_p, put_m;   // placements: fill-right arm (+P), fill-left arm (-P)
+  };
   template <int J, int Q>
-  static __device__ __forceinline__ void capture_q(const Tile<DT, S>& t, E* sOL, E* sOR, int mp, int P,
-                                                   int cl, int lane) {
+  static __device__ __forceinline__ void capture_q(const Tile<DT, S>& t, E* sOL, E* sOR, const Lanes& ln) {
     using Ps = Pos<J, Q>;
-    if (lane == ((cl + Ps::XSL / S + P) & 31)) sOL[mp * 2 * R + Q] = t.get(Ps::XSL % S);
-    if (lane == ((cl + Ps::XSR / S - P) & 31)) sOR[mp * 2 * R + Q] = t.get(Ps::XSR % S);
+    if (ln.cap_p == (Ps::XSL / S) % 32) sOL[Q] = t.get(Ps::XSL % S);
+    if (ln.cap_m == (Ps::XSR / S) % 32) sOR[Q] = t.get(Ps::XSR % S);
   }
   template <int J, int Q>
   static __device__ __forceinline__ void place_q(Tile<DT, S>& t, const E (&al)[2 * R], const E (&ar)[2 * R],
-                                                 int P, int cl, int lane) {
+                                                 const Lanes& ln) {
     using Ps = Pos<J, Q>;
-    if (lane == ((cl + Ps::XGL / S - P) & 31)) t.put(Ps::XGL % S, al[Q]);
-    if (lane == ((cl + Ps::XGR / S + P) & 31)) t.put(Ps::XGR % S, ar[Q]);
+    if (ln.put_m == (Ps::XGL / S) % 32) t.put(Ps::XGL % S, al[Q]);
+    if (ln.put_p == (Ps::XGR / S) % 32) t.put(Ps::XGR % S, ar[Q]);
   }
   template <int J, int... Qs>
-  static __device__ __forceinline__ void capture_all(const Tile<DT, S>& t, E* sOL, E* sOR, int mp, int P,
-                                                     int cl, int lane, std::integer_sequence<int, Qs...>) {
-    (capture_q<J, Qs>(t, sOL, sOR, mp, P, cl, lane), ...);
+  static __device__ __forceinline__ void capture_all(const Tile<DT, S>& t, E* sOL, E* sOR, const Lanes& ln,
+                                                     std::integer_sequence<int, Qs...>) {
+    (capture_q<J, Qs>(t, sOL, sOR, ln), ...);
   }
   template <int J, int... Qs>
   static __device__ __forceinline__ void place_all(Tile<DT, S>& t, const E (&al)[2 * R], const E (&ar)[2 * R],
-                                                   int P, int cl, int lane, std::integer_sequence<int, Qs...>) {
-    (place_q<J, Qs>(t, al, ar, P, cl, lane), ...);
+                                                   const Lanes& ln, std::integer_sequence<int, Qs...>) {
+    (place_q<J, Qs>(t, al, ar, ln), ...);
+  }
+  static __device__ __forceinline__ Lanes lanes_of(int rel, int P, bool fill, bool empty) {
+    const int rp = (rel - P) & 31, rm = (rel + P) & 31;
+    return Lanes{empty ? rp : -1, empty ? rm : -1, fill ? rp : -1, fill ? rm : -1};
   }
 
   template <int LO, int HI, class F>
@@ -190,6 +203,8 @@ struct RingImpl {
       }
       __syncwarp();
       int P = 0, j = 0;
+      const int rel = (lane - cl) & 31;
+      Lanes ln = lanes_of(rel, 0, fill, empty);
 #pragma unroll 1
       for (int mp = 0; mp < H; ++mp) {
         E al[2 * R], ar[2 * R];
@@ -200,10 +215,12 @@ struct RingImpl {
         }
         __syncwarp();
         // (the emptied window sits at offset cl + M/2: the XS* constants include M/2)
+        E* const cL = s0 + mp * 2 * R;
+        E* const cR = s1 + mp * 2 * R;
         select<0, L>(j, [&](auto JJ) {
           constexpr int J = decltype(JJ)::value;
-          if (empty) capture_all<J>(t, s0, s1, mp, P, cl, lane, std::make_integer_sequence<int, 2 * R>{});
-          if (fill) place_all<J>(t, al, ar, P, cl, lane, std::make_integer_sequence<int, 2 * R>{});
+          capture_all<J>(t, cL, cR, ln, std::make_integer_sequence<int, 2 * R>{});
+          place_all<J>(t, al, ar, ln, std::make_integer_sequence<int, 2 * R>{});
         });
         // Several sub-timesteps per step: both windows are at the same
         // level modulo Subs (h is a multiple of Subs), so one sub-timestep
@@ -216,7 +233,11 @@ struct RingImpl {
           tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, nullptr,
                                        (int)((a.lev_fill + mp) & (Subs<ST>::value - 1)));
         }
-        if (++j == L) { j = 0; ++P; }
+        if (++j == L) {
+          j = 0;
+          ++P;
+          ln = lanes_of(rel, P, fill, empty);
+        }
       }
       __syncwarp();
       if (empty) {
