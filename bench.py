@@ -53,7 +53,7 @@ OPS_PER_UPDATE_F64_HEAT = 3
 # DRAM bytes (read + write) of one swept_ring_kernel<heat, F32C, K=32> launch at N = 2^24,
 # from one ncu capture (profiles/swept_ring_kernel_heat_f32c_K32_N2p24.md).  Update it
 # whenever that kernel changes.
-RING_K32_TRAFFIC_BYTES = 268.592384e6 + 209.810432e6
+RING_K32_TRAFFIC_BYTES = 268.548864e6 + 210.693632e6
 
 
 def workload_config(n_gpus: int):
