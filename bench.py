@@ -50,10 +50,11 @@ METRIC = "cell-updates/s (N x steps / s), swept vs naive stepper, 1 GB300, at st
 UNIT = "cell-updates/s"
 OPS_PER_UPDATE_F32C_HEAT = 9     # neighbour difference (shared, 1 per point), sub, fma, TwoSum (6)
 OPS_PER_UPDATE_F64_HEAT = 3
-# DRAM bytes (read + write) of one swept_ring_kernel<heat, F32C, K=32> launch at N = 2^24,
-# from one ncu capture (profiles/swept_ring_kernel_heat_f32c_K32_N2p24.md).  Update it
-# whenever that kernel changes.
-RING_K32_TRAFFIC_BYTES = 268.548864e6 + 210.693632e6
+# DRAM bytes (read + write) of one swept_stream_kernel<heat, F32C, K=32> launch (the 38
+# full-diamond stages of one 20000-step advance at N = 2^24), from one ncu capture
+# (profiles/swept_stream_kernel_heat_f32c_K32_N2p24.md).  Update it whenever that kernel
+# changes.
+STREAM_K32_TRAFFIC_BYTES = 10.200596e9 + 10.151927e9
 
 
 def workload_config(n_gpus: int):
@@ -222,7 +223,9 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     h = plan.h
-    launches_per_step = NSTEPS // h + (2 if NSTEPS % h else 1)
+    # events around the ring launch of every advance: the dominant kernel's own duration
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_TIME_RING, 1)
+    ring_ms, launches = [], []
 
     def barrier():
         if world > 1:
@@ -238,6 +241,9 @@ def run_gpu(args):
         e1.record(stream)
         if timed_list is not None:
             timed_list.append((e0, e1))
+            n_all, n_ring, t_ring = sw.swept_plan_last_advance(plan)    # waits for the ring launch
+            launches.append((n_all, n_ring))
+            ring_ms.append(t_ring)
 
     for _ in range(args.warmup):
         one()
@@ -353,21 +359,25 @@ def run_gpu(args):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # Dominant kernel: the ring-pipelined diamond kernel (heat, compensated
-    # FP32, K = 32), 38 of the 41 launches of a step.  achieved = useful FP32
-    # operations of the whole advance / its time; the three other launches
-    # (first triangle, last fill, remainder) do less useful work per second,
-    # so this is a lower bound on the ring kernel's own rate.
-    per_launch_ops = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * h
-    avg_launch_s = (t_dev / args.steps) / launches_per_step
+    # Dominant kernel: the streamed ring kernel (heat, compensated FP32, K = 32), one
+    # launch per step running the q - 1 = 38 full-diamond stages (N x h updates each);
+    # the other three launches are the first triangle, the last fill and the remainder.
+    # Its duration comes from the library's events around it in every timed step.
+    n_all, n_ring = launches[0]
+    q = NSTEPS // h
+    per_launch_ops = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * h * (q - 1) / n_ring
+    avg_launch_s = statistics.mean(ring_ms) / 1e3 / n_ring
     peak_ops = 152 * 128 * sm_max * 1e6
-    achieved = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * NSTEPS / (t_dev / args.steps)
-    roof = {"bound": "alu", "kernel": "swept_ring_kernel<heat,f32c,K=32>",
+    achieved = per_launch_ops / avg_launch_s
+    whole = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * NSTEPS / (t_dev / args.steps)
+    roof = {"bound": "alu", "kernel": "swept_stream_kernel<heat,f32c,K=32>",
             "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops, "traffic": RING_K32_TRAFFIC_BYTES,
+            "frac": achieved / peak_ops, "traffic": STREAM_K32_TRAFFIC_BYTES,
             "traffic_unit": "DRAM bytes per launch (ncu)",
-            "algorithmic_edge_bytes_per_launch": 2 * 16 * N_POINTS,
+            "algorithmic_edge_bytes_per_launch": 2 * 16 * N_POINTS * (q - 1) / n_ring,
             "per_launch_ops": per_launch_ops, "avg_launch_ms": avg_launch_s * 1e3,
+            "launches_per_step": n_all, "ring_launches_per_step": n_ring,
+            "achieved_whole_advance": whole / 1e12, "frac_whole_advance": whole / peak_ops,
             "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"}
     cpu = time_oracle() if world == 1 else None
     naive_roof = hbm * 1e9 / 16.0
@@ -378,7 +388,7 @@ def run_gpu(args):
             "data": "synthetic", "config": workload_config(world),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N_POINTS,
                     "d2h_bytes_per_step": 8 * N_POINTS},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": sum(n for n, _ in launches),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "max_err_vs_exact": max_err,
             "compare": {"naive_f32c": naive_f32c, "swept_f64": swept_f64, "naive_f64": naive_f64,

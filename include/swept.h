@@ -160,7 +160,20 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        regime); other plans ignore it.  0 (default): off.
  *                        A wait that runs out ends the launch with the status
  *                        SWEPT_ETIMEOUT, read by swept_plan_status.
- *   SWEPT_OPT_TIMEOUT_MS budget of each persistent wait, 1..600000 ms (2000).
+ *   SWEPT_OPT_STREAM     1 (default): an advance whose ring stages (full
+ *                        diamonds on evenly tiled windows, forward schemes)
+ *                        number two or more runs them all in one cooperative
+ *                        launch, where each warp's last slot of a stage is the
+ *                        first slot of its next stage; warps then wait (bounded,
+ *                        SWEPT_OPT_TIMEOUT_MS) on their right neighbour's slot
+ *                        counter once per stage.  0: one ring launch per stage.
+ *                        A wait that runs out records SWEPT_ETIMEOUT, read by
+ *                        swept_plan_status.  Results do not depend on it.
+ *   SWEPT_OPT_TIME_RING  1: each advance records CUDA events around its ring
+ *                        launches (not while the stream is being captured),
+ *                        read by swept_plan_last_advance.  0 (default): none.
+ *   SWEPT_OPT_TIMEOUT_MS budget of each persistent or streamed wait,
+ *                        1..600000 ms (2000).
  *   SWEPT_OPT_DROP_WINDOW failure injection for the persistent advance: window
  *                        `value` never publishes its stages (a lost message),
  *                        so its neighbours' waits run out; -1 (default) none.
@@ -173,6 +186,8 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
 #define SWEPT_OPT_PERSISTENT  4
 #define SWEPT_OPT_DROP_WINDOW 5
 #define SWEPT_OPT_TIMEOUT_MS  6
+#define SWEPT_OPT_STREAM      7
+#define SWEPT_OPT_TIME_RING   8
 #define SWEPT_DIAMOND_AUTO    0
 #define SWEPT_DIAMOND_WINDOW  1
 #define SWEPT_DIAMOND_RING    2
@@ -209,10 +224,22 @@ int swept_naive_advance(swept_plan_t plan, void *u, int64_t nsteps, void *stream
 
 /*
  * swept_plan_status -- synchronise `stream` and return the device status of
- * the plan's last persistent advance: SWEPT_OK or SWEPT_ETIMEOUT (a device
- * wait ran out; the state is then undefined).  Other advances leave it OK.
+ * the plan's last persistent or streamed advance (SWEPT_OPT_PERSISTENT,
+ * SWEPT_OPT_STREAM): SWEPT_OK or SWEPT_ETIMEOUT (a device wait ran out; the
+ * state is then undefined).  Other advances leave it as it was.
  */
 int swept_plan_status(swept_plan_t plan, void *stream);
+
+/*
+ * swept_plan_last_advance -- what the plan's last swept_advance enqueued:
+ * the kernel launches (stages; a streamed ring launch counts once) in
+ * *launches, the ring launches among them in *ring_launches, and, when
+ * SWEPT_OPT_TIME_RING is on and the advance was not captured, the device time
+ * from the first ring launch's start to the last one's end in *ring_ms
+ * (waits for it); else *ring_ms = -1.  With SWEPT_OPT_GRAPH the counts are
+ * those of the captured advance.  Errors: SWEPT_EINVAL for a null argument.
+ */
+int swept_plan_last_advance(swept_plan_t plan, int64_t *launches, int64_t *ring_launches, double *ring_ms);
 
 /* ---- adjoint ----------------------------------------------------------- */
 

@@ -22,7 +22,7 @@ SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM, SWEPT_ECUDA, SWEPT_ETIMEOUT, SWEPT_ENOTSUP
 SWEPT_ETOOBIG = -6
 SWEPT_NOALLOC_MAX_N = 1 << 20
 SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS, SWEPT_OPT_GRAPH, SWEPT_OPT_PDL, SWEPT_OPT_PERSISTENT = 0, 1, 2, 3, 4
-SWEPT_OPT_DROP_WINDOW, SWEPT_OPT_TIMEOUT_MS = 5, 6
+SWEPT_OPT_DROP_WINDOW, SWEPT_OPT_TIMEOUT_MS, SWEPT_OPT_STREAM, SWEPT_OPT_TIME_RING = 5, 6, 7, 8
 SWEPT_DIAMOND_AUTO, SWEPT_DIAMOND_WINDOW, SWEPT_DIAMOND_RING = 0, 1, 2
 
 RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2, SWEPT_HEAT_RK2: 1, SWEPT_KS_RK2: 2, SWEPT_EULER: 1}
@@ -34,7 +34,7 @@ EXPORTS = (
     "swept_advance_noalloc", "swept_plan_set",
     "swept_batch_plan", "swept_batch_set", "swept_batch_info", "swept_advance_batch",
     "swept_batch_status", "swept_batch_destroy", "swept_adjoint", "swept_batch_naive_advance",
-    "swept_plan_status",
+    "swept_plan_status", "swept_plan_last_advance",
 )
 
 SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH = 0, 1, 2, 3
@@ -100,6 +100,9 @@ def load(path: str | None = None):
         L.swept_batch_naive_advance.restype = i32
         L.swept_plan_status.argtypes = [vp, vp]
         L.swept_plan_status.restype = i32
+        L.swept_plan_last_advance.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                              ctypes.POINTER(ctypes.c_double)]
+        L.swept_plan_last_advance.restype = i32
         L.swept_batch_status.argtypes = [vp, vp]
         L.swept_batch_status.restype = i32
         L.swept_batch_destroy.argtypes = [vp]
@@ -207,8 +210,18 @@ def swept_advance(plan: Plan, u, nsteps: int, stream=None):
 
 
 def swept_plan_status(plan: Plan, stream=None) -> int:
-    """Synchronise and return the device status of the last persistent advance (0 or SWEPT_ETIMEOUT)."""
+    """Synchronise and return the device status of the last persistent or streamed advance
+    (0 or SWEPT_ETIMEOUT)."""
     return int(load().swept_plan_status(plan.handle, _stream(stream)))
+
+
+def swept_plan_last_advance(plan: Plan):
+    """(kernel launches, ring launches, ring milliseconds or -1) of the plan's last advance;
+    the time needs SWEPT_OPT_TIME_RING and waits for the advance's ring launches."""
+    n, nr, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().swept_plan_last_advance(plan.handle, ctypes.byref(n), ctypes.byref(nr), ctypes.byref(ms)),
+           "swept_plan_last_advance")
+    return int(n.value), int(nr.value), float(ms.value)
 
 
 def swept_naive_advance(plan: Plan, u, nsteps: int, stream=None):

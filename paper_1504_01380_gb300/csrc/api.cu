@@ -36,7 +36,12 @@ struct swept_plan_s {
   int* status;            // its device status word
   int drop_w;             // SWEPT_OPT_DROP_WINDOW: a window that never publishes (-1: none)
   int nreg;               // uneven tiles: windows [0, nreg) are B wide, the rest B + 32r (nreg = nwin: even)
-  double timeout_s;       // SWEPT_OPT_TIMEOUT_MS / 1000: budget of each persistent wait
+  double timeout_s;       // SWEPT_OPT_TIMEOUT_MS / 1000: budget of each persistent or streamed wait
+  int stream;             // SWEPT_OPT_STREAM: ring stages of an advance in one launch
+  int time_ring;          // SWEPT_OPT_TIME_RING: events around the ring launches of each advance
+  cudaEvent_t ring_ev[2];
+  int ring_timed;         // the last advance recorded ring_ev
+  int64_t last_launches, last_ring_launches;
   cudaGraphExec_t gexec;  // captured advance (valid for g_u, g_nsteps)
   void* g_u;
   int64_t g_nsteps;
@@ -228,6 +233,7 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->pdl = 1;
   p->drop_w = -1;
   p->timeout_s = 2.0;
+  p->stream = 1;
   cudaGetDevice(&p->device);
   const size_t esize = euler ? (dtype == SWEPT_F64 ? sizeof(swept::EulerE) : sizeof(swept::EulerEF))
                               : (rk2 ? 16 : (dtype == SWEPT_F32 ? 4 : 8));
@@ -254,6 +260,10 @@ void swept_destroy(swept_plan_t p) {
   if (!p) return;
   cudaDeviceSynchronize();
   if (p->g_valid) cudaGraphExecDestroy(p->gexec);
+  if (p->time_ring) {
+    cudaEventDestroy(p->ring_ev[0]);
+    cudaEventDestroy(p->ring_ev[1]);
+  }
   if (p->edges) cudaFree(p->edges);
   if (p->red) cudaFree(p->red);
   if (p->adj) cudaFree(p->adj);
@@ -317,6 +327,34 @@ int swept_plan_set(swept_plan_t p, int option, int64_t value) {
     }
     return SWEPT_OK;
   }
+  if (option == SWEPT_OPT_TIME_RING) {
+    if (value != 0 && value != 1) return SWEPT_EINVAL;
+    if (value == p->time_ring) return SWEPT_OK;
+    cudaError_t e = cudaSuccess;
+    if (value) {
+      e = cudaEventCreate(&p->ring_ev[0]);
+      if (e == cudaSuccess) {
+        e = cudaEventCreate(&p->ring_ev[1]);
+        if (e != cudaSuccess) cudaEventDestroy(p->ring_ev[0]);
+      }
+    } else {
+      cudaEventDestroy(p->ring_ev[0]);
+      cudaEventDestroy(p->ring_ev[1]);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    p->time_ring = (int)value;
+    p->ring_timed = 0;
+    return SWEPT_OK;
+  }
+  if (option == SWEPT_OPT_STREAM) {
+    if (value != 0 && value != 1) return SWEPT_EINVAL;
+    p->stream = (int)value;
+    if (p->g_valid) {
+      cudaGraphExecDestroy(p->gexec);
+      p->g_valid = 0;
+    }
+    return SWEPT_OK;
+  }
   if (option == SWEPT_OPT_PDL) {
     if (value != 0 && value != 1) return SWEPT_EINVAL;
     p->pdl = (int)value;
@@ -350,6 +388,37 @@ bool persistent_ok(const swept_plan_s* p, int64_t levels) {
   return fits != 0;
 }
 
+// Clock cycles of one bounded wait (SWEPT_OPT_TIMEOUT_MS at the SM clock).
+long long wait_budget(const swept_plan_s* p) {
+  int dev = 0, khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (khz <= 0) khz = 2000000;
+  return (long long)(p->timeout_s * (double)khz * 1000.0);
+}
+
+// The ring stages of an advance (q - 1 full diamonds) run as one streamed
+// launch when there are at least two of them, the tiles are even, and the
+// ring is the kernel for them (with the automatic choice: more windows than
+// four per SM, where the per-window kernel is not picked instead).
+bool stream_ok(const swept_plan_s* p, int64_t q) {
+  if (!p->stream || p->nreg != p->nwin || q < 3 || p->nwin < 3 || !use_ring(p)) return false;
+  if (q - 1 > (int64_t)0x7fffffff / p->nwin) return false;    // slot counters stay in int
+  if (p->diamond == SWEPT_DIAMOND_AUTO && p->ring_warps == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (p->nwin <= 4 * sms) return false;
+    // and only where it pays (run length against residency; the ring launcher decides)
+    StageArgs a{};
+    a.nwin = p->nwin;
+    a.nstream = (int)(q - 1);
+    a.stream_query = 1;
+    return launch_ring(p, a, nullptr) == cudaSuccess;
+  }
+  return true;
+}
+
 // Enqueue the stage sequence of one advance (Section 3's stages, A5's schedule).
 int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
   const int64_t levels = p->subs * nsteps;                // sub-timesteps
@@ -366,11 +435,7 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
     pa.edge_half = p->edge_half;
     pa.flags = p->flags;
     pa.status = p->status;
-    int dev = 0, khz = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-    if (khz <= 0) khz = 2000000;
-    pa.budget = (long long)(p->timeout_s * (double)khz * 1000.0);   // per wait
+    pa.budget = wait_budget(p);                       // per wait
     pa.drop_w = p->drop_w;
     pa.q = (int)q;
     pa.rem = rem;
@@ -383,6 +448,13 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
     return cuda_status(e);
   }
   unsigned char* buf[2] = {p->edges, p->edges + p->edge_half};
+  // launch counts of this advance, and events around its ring launches
+  // (SWEPT_OPT_TIME_RING; not while the stream is being captured)
+  int64_t nlaunch = 0, nring = 0;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool timing = p->time_ring && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+                      cap == cudaStreamCaptureStatusNone;
+  p->ring_timed = 0;
   StageArgs a{};
   a.u = u;
   a.N = p->N;
@@ -393,7 +465,7 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
   // sets of Section 3); reads the edges of stage k-1, writes its own.
   const bool uneven = p->nreg != p->nwin;
   const bool ring = use_ring(p) && p->nreg > 0;
-  auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
+  auto setup = [&](int64_t k, int hv, int ht) {
     a.offset = (k & 1) ? p->B / 2 : 0;
     a.hv = hv;
     a.ht = ht;
@@ -401,16 +473,20 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
     a.eout = buf[k & 1];
     a.lev_fill = k >= 1 ? (k - 1) * H : 0;      // absolute levels (Runge-Kutta parity)
     a.lev_trap = k * H;
-    if (!uneven) {
-      if (ring && hv == p->H && ht == p->H) return launch_ring(p, a, s);
-      return launch_stage(p, a, s);
-    }
+  };
+  auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
+    setup(k, hv, ht);
+    const bool full = ring && hv == p->H && ht == p->H;
+    ++nlaunch;
+    if (full) ++nring;
+    if (!uneven) return full ? launch_ring(p, a, s) : launch_stage(p, a, s);
     // uneven tiles: the B-wide windows (ring or per window), then the wide ones
     cudaError_t e = cudaSuccess;
     if (p->nreg > 0) {
       a.nlaunch = p->nreg;
-      e = (ring && hv == p->H && ht == p->H) ? launch_ring(p, a, s) : launch_stage(p, a, s);
+      e = full ? launch_ring(p, a, s) : launch_stage(p, a, s);
       a.nlaunch = 0;
+      ++nlaunch;
     }
     if (e != cudaSuccess) return e;
     const int odd = (int)(k & 1);
@@ -429,10 +505,35 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
     if (e == cudaSuccess) e = stage(1, rem, 0);       // its V-fill
   } else {
     e = stage(0, 0, (int)H);                           // shrinking triangles
-    for (int64_t k = 1; k < q && e == cudaSuccess; ++k) e = stage(k, (int)H, (int)H);   // diamonds
+    const bool stream = stream_ok(p, q);
+    if (e == cudaSuccess && stream) {
+      // diamonds 1 .. q-1 in one streamed ring launch; its slot counters and
+      // the status word start from 0
+      setup(1, (int)H, (int)H);
+      a.nstream = (int)(q - 1);
+      a.progress = p->flags;
+      a.status = p->status;
+      a.budget = wait_budget(p);
+      e = cudaMemsetAsync(p->flags, 0, (size_t)p->nwin * sizeof(int), s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
+      if (e == cudaSuccess && timing) e = cudaEventRecord(p->ring_ev[0], s);
+      if (e == cudaSuccess) e = launch_ring(p, a, s);
+      if (e == cudaSuccess && timing) e = cudaEventRecord(p->ring_ev[1], s);
+      a.nstream = 0;
+      ++nlaunch;
+      ++nring;
+    } else {
+      const bool timed = timing && ring && !uneven && q >= 2;
+      if (e == cudaSuccess && timed) e = cudaEventRecord(p->ring_ev[0], s);
+      for (int64_t k = 1; k < q && e == cudaSuccess; ++k) e = stage(k, (int)H, (int)H);   // diamonds
+      if (e == cudaSuccess && timed) e = cudaEventRecord(p->ring_ev[1], s);
+    }
+    p->ring_timed = timing && nring > 0 && e == cudaSuccess;
     if (e == cudaSuccess) e = stage(q, (int)H, rem);  // last V-fill (+ trapezoid)
     if (e == cudaSuccess && rem > 0) e = stage(q + 1, rem, 0);
   }
+  p->last_launches = nlaunch;
+  p->last_ring_launches = nring;
   return cuda_status(e);
 }
 
@@ -656,6 +757,21 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     e = cudaMemcpyAsync(u, p->edges, bytes, cudaMemcpyDeviceToDevice, s);
   }
   return cuda_status(e);
+}
+
+int swept_plan_last_advance(swept_plan_t p, int64_t* launches, int64_t* ring_launches, double* ring_ms) {
+  if (!p || !launches || !ring_launches || !ring_ms) return SWEPT_EINVAL;
+  *launches = p->last_launches;
+  *ring_launches = p->last_ring_launches;
+  *ring_ms = -1.0;
+  if (p->time_ring && p->ring_timed) {
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(p->ring_ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ring_ev[0], p->ring_ev[1]);
+    if (e != cudaSuccess) return cuda_status(e);
+    *ring_ms = ms;
+  }
+  return SWEPT_OK;
 }
 
 int swept_plan_status(swept_plan_t p, void* stream) {

@@ -32,6 +32,14 @@ struct StageArgs {
   int64_t lev_fill = 0, lev_trap = 0;
   int pdl = 0;                 // launch with programmatic dependent launch (host side only)
   int nlaunch = 0;             // windows launched (0: nwin); uneven tiles launch the regular ones only
+  // Streamed ring launches: full-diamond stages run by one launch (0 or 1:
+  // this stage only), with the per-warp slot counters, the status word and
+  // the clock budget of each wait on a neighbouring warp.
+  int nstream = 0;
+  int stream_query = 0;        // host only: ask whether streaming pays, launch nothing
+  int* progress = nullptr;
+  int* status = nullptr;
+  long long budget = 0;
 };
 
 // Launch `kern` on `s`; with pdl, as a programmatic dependent launch (the

@@ -39,8 +39,10 @@
 
 #include <type_traits>
 
+#include "swept.h"
 #include "swept_internal.h"
 #include "swept_stage.cuh"
+#include "swept_sync.cuh"
 
 namespace swept {
 
@@ -197,6 +199,51 @@ struct RingImpl {
     __device__ __forceinline__ void done(int) const {}
   };
 
+  // The h levels of one slot: the window being filled sits at ring offset
+  // cl lanes, the one being emptied at cl + 16.  s0/s1 hold the fill's arms
+  // on entry and the emptied window's captured edges on return.  `lev` is the
+  // absolute level of the fill's first computed level (only its value modulo
+  // Subs matters: h is a multiple of Subs, so both windows of the ring are at
+  // the same sub-timestep); `wfill` the filled window (adjoint sweeps).
+  static __device__ __forceinline__ void slot_levels(Tile<DT, S>& t, const StageArgs& a, E* s0, E* s1, int lane,
+                                                     int cl, bool fill, bool empty, int64_t lev, int wfill) {
+    int P = 0, j = 0;
+    const int rel = (lane - cl) & 31;
+    Lanes ln = lanes_of(rel, 0, fill, empty);
+#pragma unroll 1
+    for (int mp = 0; mp < H; ++mp) {
+      E al[2 * R], ar[2 * R];
+#pragma unroll
+      for (int q = 0; q < 2 * R; ++q) {
+        al[q] = s0[mp * 2 * R + q];
+        ar[q] = s1[mp * 2 * R + q];
+      }
+      __syncwarp();
+      // (the emptied window sits at offset cl + M/2: the XS* constants include M/2)
+      E* const cL = s0 + mp * 2 * R;
+      E* const cR = s1 + mp * 2 * R;
+      select_j(j, [&](auto JJ) {
+        constexpr int J = decltype(JJ)::value;
+        capture_all<J>(t, cL, cR, ln, std::make_integer_sequence<int, 2 * R>{});
+        place_all<J>(t, al, ar, ln, std::make_integer_sequence<int, 2 * R>{});
+      });
+      if constexpr (ST == kKSAdj) {
+        double cf[S];
+        adjoint_coef(cf, a, lane, cl, wfill, fill, empty, mp);
+        tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, cf, 0);
+      } else {
+        (void)wfill;
+        tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, nullptr,
+                                     (int)((lev + mp) & (Subs<ST>::value - 1)));
+      }
+      if (++j == L) {
+        j = 0;
+        ++P;
+        ln = lanes_of(rel, P, fill, empty);
+      }
+    }
+  }
+
   // One warp: windows [w0, w1) of a full diamond stage (hv = ht = h).
   // sm: 2B elements of shared memory.
   static __device__ void run(const StageArgs& a, E* sm, int w0, int w1) {
@@ -232,43 +279,7 @@ struct RingImpl {
         warp_copy(s1, ein + (int64_t)wr * (2 * B), B, lane);
       }
       __syncwarp();
-      int P = 0, j = 0;
-      const int rel = (lane - cl) & 31;
-      Lanes ln = lanes_of(rel, 0, fill, empty);
-#pragma unroll 1
-      for (int mp = 0; mp < H; ++mp) {
-        E al[2 * R], ar[2 * R];
-#pragma unroll
-        for (int q = 0; q < 2 * R; ++q) {
-          al[q] = s0[mp * 2 * R + q];
-          ar[q] = s1[mp * 2 * R + q];
-        }
-        __syncwarp();
-        // (the emptied window sits at offset cl + M/2: the XS* constants include M/2)
-        E* const cL = s0 + mp * 2 * R;
-        E* const cR = s1 + mp * 2 * R;
-        select_j(j, [&](auto JJ) {
-          constexpr int J = decltype(JJ)::value;
-          capture_all<J>(t, cL, cR, ln, std::make_integer_sequence<int, 2 * R>{});
-          place_all<J>(t, al, ar, ln, std::make_integer_sequence<int, 2 * R>{});
-        });
-        // Several sub-timesteps per step: both windows are at the same
-        // level modulo Subs (h is a multiple of Subs), so one sub-timestep
-        // serves the whole ring
-        if constexpr (ST == kKSAdj) {
-          double cf[S];
-          adjoint_coef(cf, a, lane, cl, w0 + slot, fill, empty, mp);
-          tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, cf, 0);
-        } else {
-          tile_level<ST, DT, S, false>(t, a.c, lane, nullptr, nullptr, nullptr,
-                                       (int)((a.lev_fill + mp) & (Subs<ST>::value - 1)));
-        }
-        if (++j == L) {
-          j = 0;
-          ++P;
-          ln = lanes_of(rel, P, fill, empty);
-        }
-      }
+      slot_levels(t, a, s0, s1, lane, cl, fill, empty, a.lev_fill, w0 + slot);
       __syncwarp();
       if (empty) {
         const int ws = w0 + slot - 1;
@@ -280,6 +291,109 @@ struct RingImpl {
     }
     return true;
   }
+
+  // Stages k0 .. k0 + a.nstream - 1 (all full diamonds) streamed by one warp
+  // (warp g of nwarps) in one launch: the slot that empties a stage's last
+  // window fills the next stage's first, so a run of n windows costs n slots
+  // per stage instead of n + 1 (the first slot of a run only fills and the
+  // last only empties).
+  //
+  // Window ownership drifts: at stage k0 + j the warp runs windows
+  // w0 + d(j) .. w1 - 1 + d(j) (mod nwin), d(j) = (j + [k0 odd]) / 2, i.e.
+  // one window to the right at every step from an offset stage to an
+  // unshifted one.  Window w of an offset stage reads windows w and w + 1 of
+  // the previous stage, of an unshifted stage windows w - 1 and w; with the
+  // drift, every window of the warp reads windows of its own run of the
+  // previous stage, except the last, which also reads the first window of
+  // warp g + 1's run.  So the first window of a stage reads two windows that
+  // were emptied in earlier slots (n >= 3), and the one cross-warp input is
+  // waited for on warp g + 1's slot counter (a bounded wait).
+  //
+  // Edge buffers: stage k0 + j reads a.ein when j is even (else a.eout) and
+  // writes the other.  A stage's edges overwrite those of two stages back,
+  // read by the stage in between; its readers are this warp's own earlier
+  // fills and warp g + 1's first fill of that stage, which the same wait has
+  // seen finished; warp g - 1 reads only windows left of this warp's range at
+  // every stage (the drift moves the range right), whatever its lag.
+  //
+  // With a.nstream <= 1 this is the one-stage run of run() (d = 0, no wait).
+  // Returns false if a wait gave up (the status word then holds
+  // SWEPT_ETIMEOUT).
+  static __device__ bool run_stream(const StageArgs& a, E* sm, int g, int nwarps) {
+    const int lane = threadIdx.x & 31;
+    const int nw = a.nlaunch ? a.nlaunch : a.nwin;   // windows run (uneven tiles: the regular ones)
+    const int w0 = (int)(((int64_t)g * nw) / nwarps);
+    const int n = (int)(((int64_t)(g + 1) * nw) / nwarps) - w0;
+    if (n <= 0) return true;
+    const int nst = a.nstream > 1 ? a.nstream : 1;
+    const int gr = g + 1 == nwarps ? 0 : g + 1;      // the right neighbour's run length
+    const int nr = (int)(((int64_t)(gr + 1) * nw) / nwarps - ((int64_t)gr * nw) / nwarps);
+    const int odd0 = a.offset != 0;
+    E* s0 = sm;
+    E* s1 = sm + B;
+    Tile<DT, S> t;
+    t.zero();
+    const int T = nst * n;                           // windows streamed
+    int jf = 0, i_f = 0;                             // next window to fill: stage k0 + jf, run index i_f
+    int je = 0, ie = 0;                              // window being emptied
+    for (int slot = 0; slot <= T; ++slot) {
+      const bool fill = slot < T;
+      const bool empty = slot > 0;
+      const int cl = (slot & 1) ? 16 : 0;
+      if (fill) {
+        if (i_f == n - 1 && jf > 0) {
+          // warp gr's first window of stage k0 + jf - 1 is emptied in its slot
+          // (jf - 1) * nr + 1: wait until its counter has passed that slot
+          const int target = (jf - 1) * nr + 2;
+          const long long t0 = clock64();
+          bool ok = true;
+          for (int it = 0;; ++it) {
+            if (ld_relaxed(a.progress + gr) >= target) break;
+            if ((it & 63) == 63 && (clock64() - t0 > a.budget || ld_relaxed(a.status) != 0)) {
+              ok = false;
+              break;
+            }
+            __nanosleep(128);
+          }
+          fence_acq_rel();
+          if (!__all_sync(kFull, ok)) {
+            if (lane == 0) atomicCAS(a.status, 0, SWEPT_ETIMEOUT);
+            return false;
+          }
+        }
+        const bool offs = ((jf + odd0) & 1) != 0;
+        const int w = (w0 + ((jf + odd0) >> 1) + i_f) % a.nwin;
+        const int wl = offs ? w : (w == 0 ? a.nwin - 1 : w - 1);
+        const int wr = offs ? (w + 1 == a.nwin ? 0 : w + 1) : w;
+        const E* ein = static_cast<const E*>((jf & 1) ? a.eout : a.ein);
+        warp_copy(s0, ein + (int64_t)wl * (2 * B) + B, B, lane);
+        warp_copy(s1, ein + (int64_t)wr * (2 * B), B, lane);
+      }
+      __syncwarp();
+      slot_levels(t, a, s0, s1, lane, cl, fill, empty, a.lev_fill + (int64_t)jf * H, 0);
+      __syncwarp();
+      if (empty) {
+        const int w = (w0 + ((je + odd0) >> 1) + ie) % a.nwin;
+        E* eout = static_cast<E*>((je & 1) ? const_cast<void*>(a.ein) : a.eout);
+        warp_copy(eout + (int64_t)w * (2 * B), s0, B, lane);
+        warp_copy(eout + (int64_t)w * (2 * B) + B, s1, B, lane);
+        if (++ie == n) {
+          ie = 0;
+          ++je;
+        }
+      }
+      __syncwarp();
+      if (nst > 1 && lane == 0) {
+        __threadfence();
+        st_release(a.progress + g, slot + 1);
+      }
+      if (fill && ++i_f == n) {
+        i_f = 0;
+        ++jf;
+      }
+    }
+    return true;
+  }
 };
 
 // Shared memory of the ring kernel per block: 2B elements per warp.
@@ -288,8 +402,19 @@ size_t ring_smem_bytes() {
   return stage_smem_bytes(32 * K, (int)sizeof(typename DT::E));
 }
 
+// Blocks per SM that the ring's shared memory admits (2B edge elements per
+// warp; 228 KB per SM, 1 KB of it reserved per block), at most 16 (64 warps).
+// Declared as the kernels' minimum blocks per SM, it tells the register
+// allocator the budget it may use without lowering that occupancy
+// (65536 / (blocks x 128) registers per thread).
+template <class DT, int K> struct RingBlocks {
+  static constexpr int smem = kWarpsPerBlock * 2 * 32 * K * (int)sizeof(typename DT::E);
+  static constexpr int by_smem = (228 * 1024) / (smem + 1024);
+  static constexpr int value = by_smem <= 4 ? (by_smem < 1 ? 1 : by_smem) : 0;
+};
+
 template <int ST, class DT, int K>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, RingBlocks<DT, K>::value)
 swept_ring_kernel(const StageArgs a, int nwarps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
@@ -302,6 +427,19 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
   const int w0 = (int)(((int64_t)gw * nw) / nwarps);
   const int w1 = (int)(((int64_t)(gw + 1) * nw) / nwarps);
   if (w1 > w0) RingImpl<ST, DT, K>::run(a, sm, w0, w1);
+}
+
+// Several full-diamond stages in one launch (RingImpl::run_stream); a kernel
+// of its own so that the one-stage kernel keeps its register budget.
+template <int ST, class DT, int K>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, RingBlocks<DT, K>::value)
+swept_stream_kernel(const StageArgs a, int nwarps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using E = typename DT::E;
+  E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * 32 * K);
+  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (gw >= nwarps) return;
+  RingImpl<ST, DT, K>::run_stream(a, sm, gw, nwarps);
 }
 
 // Launch with `nwarps` warps; 0 picks min(resident warp slots of the GPU,
@@ -328,6 +466,53 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(swept_ring_kernel<ST, DT, K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if constexpr (ST != kKSAdj) {
+  if (a.nstream > 1) {
+    // streamed stages: the warps wait on one another, so every warp must be
+    // resident at once (a cooperative launch), with at least 3 windows each
+    e = cudaFuncSetAttribute(swept_stream_kernel<ST, DT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0, per_sm_ring = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, swept_stream_kernel<ST, DT, K>,
+                                                      kWarpsPerBlock * 32, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_ring, swept_ring_kernel<ST, DT, K>,
+                                                        kWarpsPerBlock * 32, smem);
+    if (e != cudaSuccess) return e;
+    int resident = sms * per_sm * kWarpsPerBlock;
+    if (FP64Pipe<DT>::value) {                       // one block per SM either way
+      if (resident > 4 * sms) resident = 4 * sms;
+      per_sm = per_sm_ring = 1;
+    }
+    if (nwarps <= 0 || nwarps > resident) nwarps = resident;
+    if (nwarps > nw / 3) nwarps = nw / 3;
+    if (nwarps < 1 || a.nlaunch) return cudaErrorInvalidValue;
+    if (a.stream_query) {
+      // Streaming saves each run's extra slot per stage, 1/n of the work for
+      // runs of n windows, and its kernel may hold fewer blocks per SM than
+      // the one-stage kernel (it keeps more registers).  Measured on GB300
+      // (heat, compensated FP32, N = 2^24): 7-11% faster for runs of 8-12
+      // windows; 5-9% slower for runs of 18-27 windows that cost residency.
+      const int n = (nw + nwarps - 1) / nwarps;
+      return (n <= 16 || per_sm >= per_sm_ring) ? cudaSuccess : cudaErrorNotSupported;
+    }
+    const int grid = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kWarpsPerBlock * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, swept_stream_kernel<ST, DT, K>, a, nwarps);
+  }
+  }
   if (nwarps <= 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);

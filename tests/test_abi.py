@@ -87,6 +87,9 @@ def test_null_arguments(lib):
     assert lib.swept_f32c_split(0, None, None, None) == -1
     info = (ctypes.c_int64 * 6)()
     assert lib.swept_plan_info(None, info, 6) == -1
+    n, nr, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    assert lib.swept_plan_last_advance(None, ctypes.byref(n), ctypes.byref(nr), ctypes.byref(ms)) == -1
+    assert lib.swept_plan_set(None, 7, 1) == -1
     lib.swept_destroy(None)
 
 

@@ -185,3 +185,19 @@ def test_adjoint_not_supported(cuda_lib):
     with pytest.raises(sw.SweptError) as e:
         sw.swept_adjoint(plan, u, u, 3)
     assert e.value.code == sw.SWEPT_ENOTSUP
+
+
+@pytest.mark.parametrize("dtype,B", [(F64, 64), (F32C, 128)])
+def test_streamed_ring(cuda_lib, dtype, B):
+    """Streamed ring stages for the Euler equations (four sub-timesteps per step; the
+    ring's two windows are at the same sub-timestep in every slot): 19 windows on 6 warps,
+    up to 6 streamed stages, bit-exact against the oracle."""
+    sw = cuda_lib
+    N = 19 * B
+    q, prm = state(N, 7 + B)
+    plan = sw.swept_plan(N, 1, EULER, prm, dtype, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, 2)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, 6)
+    per_stage = plan.h // 4
+    for nsteps in (3 * per_stage, 7 * per_stage + 3):
+        assert_same(run(sw, plan, q, nsteps), oracle_run(prm, q, nsteps, dtype))

@@ -84,3 +84,20 @@ def test_ks_rk2_paper_ic_full_size(cuda_lib):
         idx = (x + np.arange(-half, half + 1)) % N
         seg = oracle.advance_rk2_f64(KS_RK2, KS_PRM, u0[idx], nsteps)
         assert got[x] == seg[half], x
+
+
+@pytest.mark.parametrize("st,B", [(HEAT_RK2, 64), (KS_RK2, 128)])
+def test_rk2_streamed_ring(cuda_lib, st, B):
+    """Streamed ring stages (one launch for every full diamond) for the two-stage scheme:
+    23 windows on 5 warps, up to 7 streamed stages, bit-exact against the oracle."""
+    sw = cuda_lib
+    r = 1 if st == HEAT_RK2 else 2
+    h = B // (2 * r)
+    N = 23 * B
+    plan = sw.swept_plan(N, r, st, prm(st), sw.SWEPT_F64, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, 2)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, 5)
+    u0 = initial(st, N, 900 + B)
+    for nsteps in (2 * h, 4 * h + 1):              # 4h and 8h + 2 levels
+        want = oracle.advance_rk2_f64(st, prm(st), u0, nsteps)
+        assert np.array_equal(run(sw, plan, u0, nsteps), want), nsteps
