@@ -86,3 +86,88 @@ def test_misaligned_or_short_state_is_rejected(cuda_lib):
     sw.swept_advance(plan, u, 33)
     torch.cuda.synchronize()
     assert np.array_equal(u.cpu().numpy(), oracle.advance_f64(HEAT, [0.25], u0, 33))
+
+
+def _streamed_plan(sw, N, radius, stencil, prm, dtype, B, warps):
+    """A plan whose advances stream their diamond stages (ring forced, explicit warps)."""
+    plan = sw.swept_plan(N, radius, stencil, prm, dtype, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, warps)
+    return plan
+
+
+def test_streamed_advance_in_graphs(cuda_lib):
+    """The streamed ring launch is cooperative: captured by SWEPT_OPT_GRAPH and by the
+    caller's torch.cuda.graph, replayed twice each, the oracle's bits every time."""
+    import torch
+    sw = cuda_lib
+    N, B = 40 * 256, 256
+    u0 = workloads.uniform(N, 64)
+    nsteps = 6 * (B // 2) + 7
+    want = oracle.advance_f64(HEAT, [0.25], u0, nsteps)
+    src = torch.tensor(u0, device="cuda")
+    plan = _streamed_plan(sw, N, 1, HEAT, [0.25], F64, B, 9)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+    u = src.clone()
+    for _ in range(2):
+        u.copy_(src)
+        sw.swept_advance(plan, u, nsteps)
+        torch.cuda.synchronize()
+        assert np.array_equal(u.cpu().numpy(), want)
+    assert sw.swept_plan_status(plan) == 0
+    plan2 = _streamed_plan(sw, N, 1, HEAT, [0.25], F64, B, 9)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        sw.swept_advance(plan2, u, nsteps)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        sw.swept_advance(plan2, u, nsteps)
+    for _ in range(2):
+        u.copy_(src)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(u.cpu().numpy(), want)
+    assert sw.swept_plan_status(plan2) == 0
+
+
+def test_two_streamed_advances_at_once(cuda_lib):
+    """Two plans whose automatic choice streams, each over every resident warp slot (at
+    least 3 windows for each of 64 warps per SM), advanced at the same time on two streams:
+    a cooperative launch is all co-resident or waits, so neither times out, and both give
+    the naive stepper's bits."""
+    import torch
+    sw = cuda_lib
+    B = 256
+    nwin = 3 * 64 * torch.cuda.get_device_properties(0).multi_processor_count
+    N = nwin * B
+    ph = sw.swept_plan(N, 1, HEAT, [0.25], F32C, B)
+    pk = sw.swept_plan(N, 2, KS, KS_PRM, F32C, B)
+    uh0 = workloads.uniform(N, 65)
+    uk0 = workloads.ks_smoothed(N, 66) * 10
+    states = []
+    for u0 in (uh0, uk0):
+        hi, lo = oracle.split_f32c(u0)
+        states.append(torch.tensor(np.concatenate([hi, lo]), device="cuda"))
+    want = []
+    for plan, st, n in ((ph, states[0], 9 * 128 + 3), (pk, states[1], 9 * 64 + 5)):
+        ref = st.clone()
+        sw.swept_naive_advance(plan, ref, n)
+        want.append(ref)
+    uh, uk = states[0].clone(), states[1].clone()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    s1.wait_stream(torch.cuda.current_stream())
+    s2.wait_stream(torch.cuda.current_stream())
+    for _ in range(3):
+        with torch.cuda.stream(s1):
+            uh.copy_(states[0])
+            sw.swept_advance(ph, uh, 9 * 128 + 3, stream=s1)
+        with torch.cuda.stream(s2):
+            uk.copy_(states[1])
+            sw.swept_advance(pk, uk, 9 * 64 + 5, stream=s2)
+        torch.cuda.synchronize()
+        assert sw.swept_plan_status(ph) == 0 and sw.swept_plan_status(pk) == 0
+        assert torch.equal(uh, want[0]) and torch.equal(uk, want[1])
+    assert sw.swept_plan_last_advance(ph)[1] == 1 and sw.swept_plan_last_advance(pk)[1] == 1
