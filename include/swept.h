@@ -174,9 +174,10 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        read by swept_plan_last_advance.  0 (default): none.
  *   SWEPT_OPT_TIMEOUT_MS budget of each persistent or streamed wait,
  *                        1..600000 ms (2000).
- *   SWEPT_OPT_DROP_WINDOW failure injection for the persistent advance: window
- *                        `value` never publishes its stages (a lost message),
- *                        so its neighbours' waits run out; -1 (default) none.
+ *   SWEPT_OPT_DROP_WINDOW failure injection: in the persistent advance window
+ *                        `value`, in a streamed ring launch warp `value`, never
+ *                        publishes its progress (a lost message), so the waits
+ *                        on it run out; -1 (default) none.
  * Errors: SWEPT_EINVAL for an unknown option or value.
  */
 #define SWEPT_OPT_DIAMOND     0

@@ -514,6 +514,7 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
       a.progress = p->flags;
       a.status = p->status;
       a.budget = wait_budget(p);
+      a.drop = p->drop_w;
       e = cudaMemsetAsync(p->flags, 0, (size_t)p->nwin * sizeof(int), s);
       if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
       if (e == cudaSuccess && timing) e = cudaEventRecord(p->ring_ev[0], s);

@@ -40,6 +40,7 @@ struct StageArgs {
   int* progress = nullptr;
   int* status = nullptr;
   long long budget = 0;
+  int drop = -1;               // failure injection: this warp never publishes its slot counter
 };
 
 // Launch `kern` on `s`; with pdl, as a programmatic dependent launch (the

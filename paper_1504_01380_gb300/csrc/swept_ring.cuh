@@ -383,7 +383,7 @@ struct RingImpl {
         }
       }
       __syncwarp();
-      if (nst > 1 && lane == 0) {
+      if (nst > 1 && lane == 0 && g != a.drop) {
         __threadfence();
         st_release(a.progress + g, slot + 1);
       }

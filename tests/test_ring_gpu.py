@@ -124,3 +124,26 @@ def test_last_advance_counts_and_ring_time(cuda_lib):
     run_gpu(sw, plan, u0, 2 * h)           # q = 2: one diamond stage, timing off
     assert sw.swept_plan_last_advance(plan)[2] == -1.0
     plan.destroy()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_streamed_lost_progress_times_out_and_gpu_stays_usable(cuda_lib, dtype):
+    """A warp of a streamed ring launch whose slot counter is never published (a lost
+    message, SWEPT_OPT_DROP_WINDOW): its left neighbour's bounded wait runs out, the
+    status reads SWEPT_ETIMEOUT, and the next advance on the same context is exact."""
+    sw = cuda_lib
+    B = 128
+    N = 24 * B
+    plan = sw.swept_plan(N, 1, 0, params_of(0), dtype, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, 4)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_TIMEOUT_MS, 100)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DROP_WINDOW, 2)
+    u0 = initial(0, N, 13)
+    nsteps = 8 * plan.h + 3
+    run_gpu(sw, plan, u0, nsteps)
+    assert sw.swept_plan_status(plan) == sw.SWEPT_ETIMEOUT
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DROP_WINDOW, -1)
+    got = run_gpu(sw, plan, u0, nsteps)
+    assert sw.swept_plan_status(plan) == 0
+    assert_same(plan, got, oracle_run(0, dtype, u0, nsteps))
