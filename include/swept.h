@@ -166,7 +166,10 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        launch, where each warp's last slot of a stage is the
  *                        first slot of its next stage; warps then wait (bounded,
  *                        SWEPT_OPT_TIMEOUT_MS) on their right neighbour's slot
- *                        counter once per stage.  0: one ring launch per stage.
+ *                        counter once per stage.  With the automatic kernel
+ *                        choice (SWEPT_DIAMOND_AUTO, automatic warps) only where
+ *                        it pays: runs of at most 16 windows per warp, or no
+ *                        loss of resident blocks.  0: one ring launch per stage.
  *                        A wait that runs out records SWEPT_ETIMEOUT, read by
  *                        swept_plan_status.  Results do not depend on it.
  *   SWEPT_OPT_TIME_RING  1: each advance records CUDA events around its ring
