@@ -347,6 +347,23 @@ def run_gpu(args):
         sweep[str(tb)] = N_POINTS * NSTEPS / timed(lambda: sw.swept_advance(pb, u, NSTEPS))
         pb.destroy()
 
+    # FP64 reductions of the compensated state (sum, half sum of squares; dot with an FP64
+    # vector): bytes read over time, L2 flushed before each
+    red = {}
+    for name, what, nbytes in (("sum", sw.SWEPT_SUM, 8 * N_POINTS), ("half_sumsq", sw.SWEPT_HALF_SUMSQ, 8 * N_POINTS),
+                               ("dot", sw.SWEPT_DOT, 16 * N_POINTS)):
+        ts = []
+        for _ in range(5):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sw.swept_reduce(plan, u, what, v=u0_dev if what == sw.SWEPT_DOT else None)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        red[name] = {"bytes": nbytes, "ms": statistics.median(ts) * 1e3,
+                     "GB/s": nbytes / statistics.median(ts) / 1e9}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -396,7 +413,9 @@ def run_gpu(args):
                         "naive_hbm_roof_16B": naive_roof, "swept_over_naive_hbm_roof": value / world / naive_roof,
                         "swept_over_naive_f32c": value / world / naive_f32c,
                         "ops_per_update": {"f32c_heat": OPS_PER_UPDATE_F32C_HEAT, "f64_heat": OPS_PER_UPDATE_F64_HEAT},
-                        "tile_sweep_f32c": sweep},
+                        "tile_sweep_f32c": sweep,
+                        "reductions_f64": {k: dict(v, frac_of_measured_hbm=v["GB/s"] / hbm)
+                                           for k, v in red.items()}},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
     if world > 1:
