@@ -27,12 +27,16 @@
 // After h levels the filled window is flat and becomes the window being
 // emptied in the next slot (same offset), and the next window is filled at
 // the other offset.  A run of n windows takes n + 1 slots; the first slot
-// only fills and the last only empties.
+// only fills and the last only empties.  The streamed form (run_stream,
+// swept_stream_kernel) runs every full diamond stage of an advance in one
+// launch and joins each stage's last slot to the next stage's first, so a
+// run costs n slots per stage.
 //
 // Every boundary position is r*(level) plus a constant, so with levels in
 // phases of S/r the boundary stays in one lane and moves r registers per
 // level; the register offsets are compile-time, selected by a uniform branch
-// tree as in the per-window kernel.  The values computed are exactly those
+// tree as in the per-window kernel (a switch for the compensated KS ring,
+// measured faster there).  The values computed are exactly those
 // of the per-window kernel (same expression per point, only the order of
 // independent updates changes), so results are bit-identical.
 #pragma once
