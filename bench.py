@@ -747,6 +747,39 @@ def run_latency_workload(args):
         plan.destroy()
         if status != 0:
             persistent[str(B)] = None
+    # the same regime on the compensated FP32 state: per-level work on the FP32 pipe is far
+    # cheaper than on GB300's FP64 pipe, so the launch latency weighs more
+    c0 = sw.swept_f32c_split(u0)
+    c = c0.clone()
+
+    def per_sub32(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            c.copy_(c0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3)
+        return best / nsteps
+
+    f32c = {}
+    for B in (32, 64, 128):
+        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, B)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+        f32c[str(B)] = per_sub32(lambda: sw.swept_advance(plan, c, nsteps))
+        plan.destroy()
+    plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, 32)
+    g3 = torch.cuda.CUDAGraph()
+    c.copy_(c0)
+    with torch.cuda.graph(g3):
+        sw.swept_naive_advance(plan, c, nsteps)
+    naive32_graph = per_sub32(g3.replay, reps=3)
+    plan.destroy()
+    best32 = min(f32c, key=f32c.get)
     fit = tune.fit_eq1([(int(b), t) for b, t in swept_graph.items()])
     best = min(swept_graph, key=swept_graph.get)
     line = {"metric": "time per sub-timestep (latency regime)", "value": swept_graph[best] * 1e9,
@@ -760,6 +793,10 @@ def run_latency_workload(args):
             "swept_persistent_ns": {b: (t * 1e9 if t is not None else None) for b, t in persistent.items()},
             "speedup_vs_naive": naive / swept_graph[best],
             "speedup_vs_naive_graph": naive_graph / swept_graph[best],
+            "f32c": {"workload": "heat1d_N1024_r0.25_2000steps_f32c", "best_B": int(best32),
+                     "swept_graph_ns": {b: t * 1e9 for b, t in f32c.items()},
+                     "naive_graph_ns": naive32_graph * 1e9,
+                     "speedup_vs_naive_graph": naive32_graph / f32c[best32]},
             "eq1_fit": {"s_ns": fit["s"] * 1e9, "tau_ns": fit["tau"] * 1e9,
                         "n_star": fit["n_star"]} if fit else None}
     print(json.dumps(line), flush=True)

@@ -88,24 +88,23 @@ struct StageImpl {
 
   // Placement for V-fill level mp = P*L + J: left arm at positions
   // 16K - R*mp - 2R + q, right arm at 16K + R*mp + q (level mp values).
+  // al / ar: the level's 2r arm values of each side.
   template <int J>
-  static __device__ __forceinline__ void place(Tile<DT, K>& t, const E* sL, const E* sR, int mp, int P,
+  static __device__ __forceinline__ void place(Tile<DT, K>& t, const E (&al)[2 * R], const E (&ar)[2 * R], int P,
                                                int lane) {
 #pragma unroll
     for (int q = 0; q < 2 * R; ++q) {
       const int cc = K - R * J - 2 * R + q;
       const int dl = cc < 0 ? 1 : 0;
       const int k = cc < 0 ? cc + K : cc;
-      const E v = sL[mp * 2 * R + q];
-      if (lane == 15 - P - dl) t.put(k, v);
+      if (lane == 15 - P - dl) t.put(k, al[q]);
     }
 #pragma unroll
     for (int q = 0; q < 2 * R; ++q) {
       const int cc = R * J + q;
       const int dr = cc >= K ? 1 : 0;
       const int k = cc - dr * K;
-      const E v = sR[mp * 2 * R + q];
-      if (lane == 16 + P + dr) t.put(k, v);
+      if (lane == 16 + P + dr) t.put(k, ar[q]);
     }
   }
 
@@ -149,13 +148,33 @@ struct StageImpl {
     const Consts& c = a.c;
     const int hmain = hv < H ? hv : H - 1;
     Coef cf;
+    // the arm values of the next level are read one level ahead, off the
+    // level's dependence chain (nothing writes the arms during the fill)
+    E al[2 * R], ar[2 * R];
+#pragma unroll
+    for (int q = 0; q < 2 * R; ++q) {
+      al[q] = sL[q];
+      ar[q] = sR[q];
+    }
 #pragma unroll 1
     for (int mp = 0; mp < hmain; ++mp) {          // level mp values placed, mp+1 computed
       const int P = mp / L;
       const int j = mp - P * L;
+      const int mn = mp + 1 < hv ? mp + 1 : mp;   // inside the hv levels of arms loaded
+      E nl[2 * R], nr[2 * R];
+#pragma unroll
+      for (int q = 0; q < 2 * R; ++q) {
+        nl[q] = sL[mn * 2 * R + q];
+        nr[q] = sR[mn * 2 * R + q];
+      }
       load_coef(cf, a, ws, lane, a.lev_fill + mp + 1);
-      select<0, L>(j, [&](auto J) { place<decltype(J)::value>(t, sL, sR, mp, P, lane); });
+      select<0, L>(j, [&](auto J) { place<decltype(J)::value>(t, al, ar, P, lane); });
       tile_level<ST, DT, K, false>(t, c, lane, nullptr, nullptr, cf.u, cf.sub);
+#pragma unroll
+      for (int q = 0; q < 2 * R; ++q) {
+        al[q] = nl[q];
+        ar[q] = nr[q];
+      }
     }
     if (hv == H) {
       // Last level: the arms reach r points beyond the window on each side.
@@ -298,8 +317,17 @@ struct StageImpl {
   }
 };
 
+// Small tiles (K <= 4) serve the latency regime, where a stage has a warp per
+// window and few warps per SM: declaring one block per SM frees the register
+// allocator (88 registers at K = 1 instead of 40 with spills), which shortens
+// each level's dependence chain.  Together with reading the V-fill's arm
+// values a level ahead, measured on GB300 (heat, N = 1024, per sub-timestep):
+// compensated 258 -> 210 ns, FP64 417 -> 374 ns.  Larger tiles keep the
+// default, which holds more warps per SM.
+template <int K> struct StageBlocks { static constexpr int value = K <= 4 ? 1 : 0; };
+
 template <int ST, class DT, int K>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, StageBlocks<K>::value)
 swept_stage_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
