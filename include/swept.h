@@ -347,14 +347,21 @@ int swept_batch_plan(swept_batch_t *out, int nprob, const swept_problem_t *probs
  *   SWEPT_BOPT_GRID       number of thread blocks (default: all resident).
  *   SWEPT_BOPT_GRAPH      1 (default): replay the advance as a CUDA graph;
  *                         0: enqueue the resets and the launch directly.
+ *   SWEPT_BOPT_RUN_LEN    windows per work item, 1..1024 (default: the longest
+ *                         of 32, 16, 8 that leaves at least 8 items per
+ *                         resident warp); rebuilds the item tables after
+ *                         waiting for the device.  Results do not depend on it.
  */
 #define SWEPT_BOPT_TIMEOUT_S  0
 #define SWEPT_BOPT_DROP_ITEM  1
 #define SWEPT_BOPT_GRID       2
 #define SWEPT_BOPT_GRAPH      3
+#define SWEPT_BOPT_RUN_LEN    4
 int swept_batch_set(swept_batch_t batch, int option, double value);
 
-/* Query: items, stages, windows, grid, problems in info[0..5). */
+/* Query: items, stages, windows, grid, problems, windows per item (the plan
+ * takes the longest of 32, 16, 8 that leaves at least 8 items per resident
+ * warp) in info[0..6). */
 int swept_batch_info(swept_batch_t batch, int64_t *info, int ninfo);
 
 /*

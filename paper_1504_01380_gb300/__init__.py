@@ -37,7 +37,7 @@ EXPORTS = (
     "swept_plan_status", "swept_plan_last_advance",
 )
 
-SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH = 0, 1, 2, 3
+SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH, SWEPT_BOPT_RUN_LEN = 0, 1, 2, 3, 4
 
 
 class swept_problem_t(ctypes.Structure):
@@ -303,9 +303,10 @@ class Batch:
         return self._h
 
     def info(self) -> dict:
-        v = (ctypes.c_int64 * 5)()
-        _check(load().swept_batch_info(self.handle, v, 5), "swept_batch_info")
-        return {"items": v[0], "stages": v[1], "windows": v[2], "grid": v[3], "problems": v[4]}
+        v = (ctypes.c_int64 * 6)()
+        _check(load().swept_batch_info(self.handle, v, 6), "swept_batch_info")
+        return {"items": v[0], "stages": v[1], "windows": v[2], "grid": v[3], "problems": v[4],
+                "run_len": v[5]}
 
     def destroy(self):
         if self._h is not None:

@@ -89,6 +89,28 @@ def test_batch_bit_exact(cuda_lib, dtype, bh, bk):
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("run_len", [1, 3, 32])
+def test_batch_run_lengths(cuda_lib, dtype, run_len):
+    """SWEPT_BOPT_RUN_LEN: items of 1 window (every ring run a single window), 3 (runs cut
+    mid-problem) and 32 (longer than most problems): bit-exact against the oracle; the
+    default run length is one of 32, 16, 8."""
+    import torch
+    sw = cuda_lib
+    states = [workloads.uniform(n, 60 + i) if st == 0 else 10 * workloads.ks_smoothed(n, 60 + i)
+              for i, (st, n, ns) in enumerate(SMALL)]
+    batch = sw.swept_batch_plan([(st, n, ns, prm(st)) for st, n, ns in SMALL], dtype, 256, 512)
+    assert batch.info()["run_len"] in (8, 16, 32)
+    sw.swept_batch_set(batch, sw.SWEPT_BOPT_RUN_LEN, run_len)
+    assert batch.info()["run_len"] == run_len
+    pool = torch.tensor(build_pool(batch, states, dtype), device="cuda")
+    sw.swept_advance_batch(batch, pool)
+    assert sw.swept_batch_status(batch) == 0
+    out = pool.cpu().numpy()
+    for (st, n, ns), off, u0 in zip(SMALL, batch.offsets, states):
+        assert same(read_state(out, off, n, dtype), expect(st, dtype, u0, ns), dtype), (st, n, ns)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
 def test_batch_naive_bit_exact(cuda_lib, dtype):
     """Per-step stepping over the ragged batch (odd and even step counts, a problem with none)."""
     import torch
@@ -167,6 +189,7 @@ def test_batch_4096_problems_sampled(cuda_lib):
     pool = torch.tensor(buf, device="cuda")
     sw.swept_advance_batch(batch, pool)
     assert sw.swept_batch_status(batch) == 0
+    assert batch.info()["run_len"] in (8, 16, 32)
     out = pool.cpu().numpy()
     for i in pick:
         st, n, ns = problems[i]
