@@ -119,8 +119,15 @@ __device__ __forceinline__ bool batch_item(const StageArgs& a, typename DT::E* s
   return true;
 }
 
+// Blocks per SM the batch kernel declares for the compensated state: 5 (a
+// budget of 102 registers, of which it uses 96 with a few spills; the
+// allocator would otherwise take 120 and leave 4 blocks).  Measured on GB300, 4096 problems, B = 256 / 512: 4 blocks
+// 1.53e12, 5 blocks 1.58e12, 6 blocks (80 registers) 1.39e12 cell-updates/s.
+template <class DT> struct BatchBlocks { static constexpr int value = 0; };
+template <> struct BatchBlocks<F32C> { static constexpr int value = 5; };
+
 template <class DT, int KH, int KK>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, BatchBlocks<DT>::value)
 swept_batch_kernel(const BatchArgs ba) {
   using E = typename DT::E;
   constexpr int BMAX = 32 * (KH > KK ? KH : KK);
