@@ -54,7 +54,7 @@ OPS_PER_UPDATE_F64_HEAT = 3
 # full-diamond stages of one 20000-step advance at N = 2^24), from one ncu capture
 # (profiles/swept_stream_kernel_heat_f32c_K32_N2p24.md).  Update it whenever that kernel
 # changes.
-STREAM_K32_TRAFFIC_BYTES = 10.200596e9 + 10.151927e9
+STREAM_K32_TRAFFIC_BYTES = 10.202137e9 + 10.150293e9
 
 
 def workload_config(n_gpus: int):
