@@ -171,3 +171,30 @@ def test_two_streamed_advances_at_once(cuda_lib):
         assert sw.swept_plan_status(ph) == 0 and sw.swept_plan_status(pk) == 0
         assert torch.equal(uh, want[0]) and torch.equal(uk, want[1])
     assert sw.swept_plan_last_advance(ph)[1] == 1 and sw.swept_plan_last_advance(pk)[1] == 1
+
+
+def test_automatic_stream_choice_under_graph_capture(cuda_lib):
+    """With the automatic kernel choice the streamed launch is decided (an occupancy query)
+    while SWEPT_OPT_GRAPH captures the advance: the replayed graph streams its diamonds
+    and gives the naive stepper's bits, twice."""
+    import torch
+    sw = cuda_lib
+    B = 256
+    nwin = 4 * torch.cuda.get_device_properties(0).multi_processor_count + 24
+    N = nwin * B
+    u0 = workloads.uniform(N, 67)
+    hi, lo = oracle.split_f32c(u0)
+    src = torch.tensor(np.concatenate([hi, lo]), device="cuda")
+    plan = sw.swept_plan(N, 1, HEAT, [0.25], F32C, B)
+    nsteps = 7 * plan.h + 3
+    ref = src.clone()
+    sw.swept_naive_advance(plan, ref, nsteps)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+    u = src.clone()
+    for _ in range(2):
+        u.copy_(src)
+        sw.swept_advance(plan, u, nsteps)
+        torch.cuda.synchronize()
+        assert torch.equal(u, ref)
+        assert sw.swept_plan_status(plan) == 0
+    assert sw.swept_plan_last_advance(plan)[1] == 1      # counts of the captured advance
