@@ -6,7 +6,9 @@ Workload: 1D heat, periodic, N = 2^24 points, r = 1/4, 20000 sub-timesteps
 per step, compensated FP32 state, tile B = 1024 (the fastest of the tile
 sweep B in {64, ..., 1024}, which is reported too); u0 = uniform[-1,1] noise
 plus 16 low modes.  One "step" is one swept_advance of the whole field
-through all 20000 sub-timesteps (q + 2 = 41 stage launches).
+through all 20000 sub-timesteps: 41 stages in 4 kernel launches (the first
+triangle, one streamed launch for the 38 full diamonds, the last fill, the
+remainder stage).
 
 Metric: cell-updates/s = N * nsteps / time.  Every step starts from the same
 device-resident input (restored outside the timed events); L2 is flushed
@@ -14,7 +16,9 @@ between steps (a 256 MiB write), also outside the timed events.
 
 Printed as one JSON line: the device-timed value, the end-to-end value
 through the public API with host buffers, the roofline of the dominant
-kernel, the CPU oracle baseline and the SM clocks seen during the run.
+kernel (its duration from CUDA events the library records around it in
+every timed step), the CPU oracle baseline and the SM clocks seen during the
+run.
 Also measured (outside the timed region, one step each): the naive per-step
 stepper and the FP64 state, and the compensated result's max error against
 the exact Fourier solution.

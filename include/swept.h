@@ -207,9 +207,10 @@ int swept_plan_set(swept_plan_t plan, int option, int64_t value);
  * previous stage's (the alternating point sets of Section 3), started from
  * the V of leading edges that the two neighbouring triangles wrote to the
  * plan's edge buffer.  nsteps = q*h + rem (h = B/(2 radius)) takes q + 1
- * launches when rem == 0, q + 2 otherwise (the last stage ends with a
+ * stages when rem == 0, q + 2 otherwise (the last stage ends with a
  * trapezoid of height rem and its fill).  Full diamond stages run on the
- * kernel chosen by SWEPT_OPT_DIAMOND.
+ * kernel chosen by SWEPT_OPT_DIAMOND; with SWEPT_OPT_STREAM they run as one
+ * launch, so an advance is as few as 4 kernel launches.
  *   u       device, state layout of the plan's dtype, overwritten in place.
  *   nsteps  >= 0; 0 is a no-op.
  * Errors: SWEPT_EINVAL (null plan/u, nsteps < 0), SWEPT_ECUDA.

@@ -3,7 +3,9 @@
 // The plan owns the device scratch: the leading-edge double buffer (the
 // "messages" of Section 3, written by one stage and read by the next) and
 // the reduction partials.  swept_advance turns nsteps into the stage
-// schedule and enqueues one stage kernel per stage on the caller's stream.
+// schedule and enqueues it on the caller's stream: the first triangle, the
+// full diamonds (one streamed ring launch, or one launch per stage), the
+// last fill and the remainder stage.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>

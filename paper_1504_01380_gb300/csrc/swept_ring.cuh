@@ -197,7 +197,7 @@ struct RingImpl {
     }
   }
 
-  // Hooks of a run without dependences (one launch per stage).
+  // Hooks of a run without dependences (one stage per launch).
   struct NoHooks {
     __device__ __forceinline__ bool ready(int) const { return true; }
     __device__ __forceinline__ void done(int) const {}
