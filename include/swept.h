@@ -62,7 +62,7 @@ extern "C" {
  * and in the edge buffers.  Same parameters as the forward-Euler stencils. */
 #define SWEPT_HEAT_RK2  2
 #define SWEPT_KS_RK2    3
-/* Euler equations of gas dynamics (Section 7), FP64 only, radius 1:
+/* Euler equations of gas dynamics (Section 7), FP64 or SWEPT_F32C, radius 1:
  * q = (rho, m, E), p = (gamma - 1)(E - m^2/(2 rho)); second-order finite
  * volumes with minmod-limited slopes, interface flux = mean physical flux
  * minus the spectral radius of the Roe matrix times the jump, midpoint rule.
@@ -82,7 +82,8 @@ extern "C" {
 #define SWEPT_EINVAL    -1   /* bad argument: sizes, radius, null pointer   */
 #define SWEPT_ENOMEM    -2   /* device allocation failed                    */
 #define SWEPT_ECUDA     -3   /* a CUDA call or kernel launch failed         */
-#define SWEPT_ETIMEOUT  -4   /* a device-side wait ran out (batched launch) */
+#define SWEPT_ETIMEOUT  -4   /* a device-side wait ran out (batched,
+                                persistent or streamed launch)              */
 #define SWEPT_ENOTSUP   -5   /* combination not built into this library     */
 #define SWEPT_ETOOBIG   -6   /* problem larger than swept_advance_noalloc's
                                 fixed scratch (N > SWEPT_NOALLOC_MAX_N)     */
@@ -141,7 +142,9 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        streams a run of windows, overlapping the V-fill of
  *                        one with the triangle of the previous).
  *   SWEPT_OPT_RING_WARPS warps of a ring launch; 0 = min(resident warp slots,
- *                        N/B/2), and at most 4 per SM for FP64 states.
+ *                        N/B/2), and at most 4 per SM for FP64 states.  A
+ *                        streamed launch takes at most the resident warps and
+ *                        at most N/B/3 (3 windows per warp or more).
  *   SWEPT_OPT_GRAPH      1: swept_advance captures its stage sequence into a
  *                        CUDA graph on the first call for a given (u, nsteps)
  *                        and replays it afterwards (fewer host launches: the
@@ -154,7 +157,8 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        device, hiding part of the launch gap; 0: plain launches.
  *   SWEPT_OPT_PERSISTENT 1: forward-Euler heat and KS advances with K <= 8 whose
  *                        windows can all be resident at once run every stage
- *                        in one launch, each warp waiting (bounded, 2 s) on
+ *                        in one launch, each warp waiting (bounded by
+ *                        SWEPT_OPT_TIMEOUT_MS, default 2 s) on
  *                        device flags for the two windows it reads from before
  *                        each stage: no stage boundary at all (the latency
  *                        regime); other plans ignore it.  0 (default): off.
