@@ -1,11 +1,12 @@
 """Benchmark of the swept-rule hot path on one GB300 (or N independent replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload heat|ks|batch|adjoint|latency|ks_rk2|euler]
 
-Workload: 1D heat, periodic, N = 2^24 points, r = 1/4, 20000 sub-timesteps
-per step, compensated FP32 state, tile B = 1024 (the fastest of the tile
-sweep B in {64, ..., 1024}, which is reported too); u0 = uniform[-1,1] noise
-plus 16 low modes.  One "step" is one swept_advance of the whole field
+Headline workload: 1D heat, periodic, N = 2^24 points, r = 1/4, 20000
+sub-timesteps per step, compensated FP32 state, tile B = 1024 (the fastest of
+the tile sweep B in {64, ..., 1024}, which is reported too); u0 = uniform[-1,1]
+noise plus 16 low modes.  One "step" is one swept_advance of the whole field
 through all 20000 sub-timesteps: 41 stages in 4 kernel launches (the first
 triangle, one streamed launch for the 38 full diamonds, the last fill, the
 remainder stage).
@@ -18,21 +19,39 @@ Printed as one JSON line: the device-timed value, the end-to-end value
 through the public API with host buffers, the roofline of the dominant
 kernel (its duration from CUDA events the library records around it in
 every timed step), the CPU oracle baseline and the SM clocks seen during the
-run.
-Also measured (outside the timed region, one step each): the naive per-step
-stepper and the FP64 state, and the compensated result's max error against
-the exact Fourier solution.
+run.  On one GPU the line also carries:
+  * peaks     -- the measured FP32 and FP64 arithmetic rates (swept_probe_alu),
+                 each with the median SM clock sampled while it ran: the
+                 denominators of every roofline fraction below;
+  * reports   -- the other workloads, each with its error against the oracle
+                 (or a closed form), its dominant kernel's time and its
+                 fraction of the measured peak:
+                   heat_c1_f64  the headline field in FP64, swept and naive;
+                   latency_c0   heat, N = 1024, 2000 steps, FP64 (the latency
+                                regime of Sections 4 and 6);
+                   ks_c2        Kuramoto-Sivashinsky, N = 2^22, 50000 steps;
+                   batch_c3     4096 ragged problems in one persistent launch;
+                   adjoint_c4   the KS gradient, N = 2^20, 20000 steps, with 32
+                                finite-difference directions.
+Algorithmic counts follow the hot-path scope's figures: compensated FP32
+heat 11 and KS 22 operations per cell-update against the measured FP32
+instruction rate (an add, mul or fma is one operation); FP64 heat 5 and KS 16
+FLOP per cell-update against twice the measured FP64 fma rate (an fma is two
+FLOP).  The counts the kernels actually execute are given beside them.
 
 --impl reference times the CPU oracle (the plain per-step definition, in
 C with OpenMP on the host cores) on a bounded sample of the same workload.
 Multi-GPU (torchrun): every rank runs its own replica (the single-problem
-path has no cross-GPU exchange); the max time over ranks is reported.
+path has no cross-GPU exchange); the max time over ranks is reported; the
+peaks and reports are measured on one GPU only.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -52,13 +71,18 @@ TILE_B = 1024
 HEAT_R = 0.25
 METRIC = "cell-updates/s (N x steps / s), swept vs naive stepper, 1 GB300, at stated error"
 UNIT = "cell-updates/s"
-OPS_PER_UPDATE_F32C_HEAT = 9     # neighbour difference (shared, 1 per point), sub, fma, TwoSum (6)
-OPS_PER_UPDATE_F64_HEAT = 3
-# DRAM bytes (read + write) of one swept_stream_kernel<heat, F32C, K=32> launch (the 38
-# full-diamond stages of one 20000-step advance at N = 2^24), from one ncu capture
-# (profiles/swept_stream_kernel_heat_f32c_K32_N2p24.md).  Update it whenever that kernel
-# changes.
-STREAM_K32_TRAFFIC_BYTES = 10.202137e9 + 10.150293e9
+# Algorithmic work per cell-update (the hot-path scope's figures) and what the kernels execute.
+ALGO_OPS_F32C = {"heat": 11, "ks": 22}        # FP32 operations (add/sub/mul/fma = 1)
+ALGO_FLOP_F64 = {"heat": 5, "ks": 16}         # FP64 FLOP (fma = 2)
+EXEC_OPS_F32C = {"heat": 9, "ks": 16}         # instructions of the compensated cores per update
+EXEC_OPS_F64 = {"heat": 3, "ks": 9}
+NOMINAL_SMS, NOMINAL_FP32_LANES = 152, 128
+# Sources that define the headline kernel (swept_stream_kernel<heat, F32C, 32>): the DRAM
+# traffic of a committed ncu summary is used only while their digest matches the one the
+# summary records.
+HEADLINE_SOURCES = ("swept_ring.cuh", "swept_stage.cuh", "swept_device.cuh", "swept_sync.cuh",
+                    "swept_internal.h", "stage_heat_f32c.cu")
+HEADLINE_PROFILE = os.path.join(ROOT, "profiles", "swept_stream_kernel_heat_f32c_K32_N2p24.md")
 
 
 def workload_config(n_gpus: int):
@@ -118,38 +142,151 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, f[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
+        lines = open(self.path).read().splitlines()
         os.unlink(self.path)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return parse_clock_lines(lines)
+
+
+def parse_clock_lines(lines):
+    """Median SM clock, max clock and the throttle reasons seen in nvidia-smi CSV lines."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for name, val in zip(names, f[5:9]):
+            if val.lower() == "active":
+                reasons.add(name)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+            "reasons": sorted(reasons)}
+
+
+def measured_peaks_file() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 
 
 def measured_hbm_gbs() -> float:
-    """Measured copy bandwidth of this GPU pool (GB/s); 6800 when the file is absent."""
+    """Measured copy bandwidth of this GPU pool (GB/s); 6800 (the fallback) when the file is absent."""
+    return float(measured_peaks_file().get("hbm_gbs", 6800.0))
+
+
+# ------------------------------------------------- committed ncu figures
+def source_digest(names=HEADLINE_SOURCES) -> str:
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_1504_01380_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(path: str = HEADLINE_PROFILE, names=HEADLINE_SOURCES):
+    """DRAM bytes (read + write) per launch from a committed ncu summary, or None when the
+    summary is missing, carries no digest, or was taken from other kernel sources."""
     try:
-        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
-    except (OSError, ValueError):
-        return 6800.0
+        text = open(path).read()
+    except OSError:
+        return None, "no committed capture"
+    m = re.search(r"source digest:\s*`?([0-9a-f]{16})", text)
+    if not m:
+        return None, "capture records no source digest"
+    if m.group(1) != source_digest(names):
+        return None, "kernel sources changed since the capture"
+    rd = re.search(r"dram__bytes_read\.sum\s*=\s*([0-9.]+)\s*Gbyte", text)
+    wr = re.search(r"dram__bytes_write\.sum\s*=\s*([0-9.]+)\s*Gbyte", text)
+    if not rd or not wr:
+        return None, "capture has no DRAM byte counts"
+    return (float(rd.group(1)) + float(wr.group(1))) * 1e9, "ncu capture of the current sources"
+
+
+# ---------------------------------------------------------- GPU timing
+def cuda_time(fn, stream=None):
+    """Seconds of fn() on the device: CUDA events on the current stream, synchronised."""
+    import torch
+    s = stream or torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def measure_alu_peaks(dev_index: int) -> dict:
+    """FP32 and FP64 operation rates of this GPU (swept_probe_alu: dependency-free chains over
+    every SM), each the best of five launches of about 100 ms, with the SM clocks sampled while
+    that probe ran."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    out = {}
+    kinds = (("f32_fma", sw.SWEPT_PROBE_F32_FMA), ("f32_add", sw.SWEPT_PROBE_F32_ADD),
+             ("f64_fma", sw.SWEPT_PROBE_F64_FMA), ("f64_add", sw.SWEPT_PROBE_F64_ADD))
+    for name, kind in kinds:
+        it = 64
+        ops = 0.0
+        while True:                                  # size one launch to about 100 ms
+            t = cuda_time(lambda: sw.swept_probe_alu(kind, it))
+            if t > 0.02 or it > (1 << 34):
+                break
+            it *= 4
+        it = max(1, int(it * 0.1 / max(t, 1e-6)))
+        with ClockSampler(dev_index) as clk:
+            best = 0.0
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ops = sw.swept_probe_alu(kind, it)
+                b.record()
+                torch.cuda.synchronize()
+                best = max(best, ops / (a.elapsed_time(b) / 1e3))
+        c = clk.summary()
+        out[name] = {"ops_per_s": best, "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")}
+    out["fp32_ops_per_s"] = max(out["f32_fma"]["ops_per_s"], out["f32_add"]["ops_per_s"])
+    out["fp64_flop_per_s"] = 2.0 * out["f64_fma"]["ops_per_s"]
+    out["how"] = ("swept_probe_alu: 8 independent add or fma chains per thread, every SM at full "
+                  "residency; best of 5 launches of ~100 ms; an add or fma is one operation, FP64 "
+                  "FLOP/s = 2 x the fma rate")
+    return out
+
+
+def peak_block(peaks, kind: str):
+    """(peak, unit, source) for the roofline: 'fp32' operations/s or 'fp64' FLOP/s, measured."""
+    sm_max = float(measured_peaks_file().get("sm_max_mhz", 2070.0))
+    if kind == "fp32":
+        nominal = NOMINAL_SMS * NOMINAL_FP32_LANES * sm_max * 1e6
+        if peaks:
+            p = peaks["fp32_ops_per_s"]
+            clk = peaks["f32_fma"]["sm_mhz"]
+            return p, "FP32 ops/s", f"measured: swept_probe_alu FP32 chains at {clk} MHz", nominal
+        return nominal, "FP32 ops/s", f"nominal: 152 SMs x 128 lanes x {sm_max:.0f} MHz", nominal
+    if peaks:
+        clk = peaks["f64_fma"]["sm_mhz"]
+        return peaks["fp64_flop_per_s"], "FP64 FLOP/s", f"measured: swept_probe_alu FP64 fma chains x 2 at {clk} MHz", None
+    return None, "FP64 FLOP/s", "not measured", None
+
+
+def roofline(work_per_s: float, peak, unit: str, source: str, **extra):
+    d = {"bound": "alu", "achieved": work_per_s / 1e12, "peak": (peak / 1e12) if peak else None,
+         "unit": "T" + unit, "frac": (work_per_s / peak) if peak else None, "peak_source": source}
+    d.update(extra)
+    return d
 
 
 # ------------------------------------------------------------ CPU oracle
 def time_oracle(target_s: float = 15.0):
-    """The oracle (compensated FP32 per-step stepping, OpenMP) on a bounded sample."""
+    """The oracle (compensated FP32 per-step stepping, OpenMP) on a bounded sample of the
+    headline field; also returns the sample's result and step count, which the GPU path must
+    reproduce bit for bit."""
     import oracle
     u0 = workloads.heat_noise_modes(N_POINTS)
     hi, lo = oracle.split_f32c(u0)
@@ -160,16 +297,17 @@ def time_oracle(target_s: float = 15.0):
     dt = max(time.perf_counter() - t0, 1e-6) / 8
     steps = max(2, min(NSTEPS, int(target_s / dt)))
     t0 = time.perf_counter()
-    oracle.advance_f32c(oracle.HEAT, [HEAT_R], hi, lo, steps, threads)
+    out = oracle.advance_f32c(oracle.HEAT, [HEAT_R], hi, lo, steps, threads)
     el = time.perf_counter() - t0
     # the same oracle on one core, a shorter sample
     steps1 = max(1, min(steps, int(2.0 / (dt * threads))))
     t0 = time.perf_counter()
     oracle.advance_f32c(oracle.HEAT, [HEAT_R], hi, lo, steps1, 1)
     el1 = time.perf_counter() - t0
-    return {"value": N_POINTS * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"N=2^24, first {steps} of 20000 sub-timesteps, {el:.1f} s",
-            "one_core": {"value": N_POINTS * steps1 / el1, "sample": f"N=2^24, {steps1} sub-timesteps"}}
+    return ({"value": N_POINTS * steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+             "sample": f"N=2^24, first {steps} of 20000 sub-timesteps, {el:.1f} s",
+             "one_core": {"value": N_POINTS * steps1 / el1, "sample": f"N=2^24, {steps1} sub-timesteps"}},
+            steps, out)
 
 
 def run_reference(args):
@@ -206,6 +344,15 @@ def run_reference(args):
     return 0
 
 
+def exact_heat(u0: np.ndarray, r: float, nsteps: int) -> np.ndarray:
+    """Closed form of periodic forward-Euler heat stepping: Fourier mode k is multiplied by
+    g_k = 1 - 4 r sin^2(pi k / N) per step."""
+    n = u0.size
+    k = np.arange(n // 2 + 1)
+    g = 1.0 - 4.0 * r * np.sin(np.pi * k / n) ** 2
+    return np.fft.irfft(np.fft.rfft(u0) * g ** nsteps, n)
+
+
 # ------------------------------------------------------------------ GPU
 def run_gpu(args):
     import torch
@@ -218,6 +365,9 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     import paper_1504_01380_gb300 as sw
     sw.load()
+
+    # measured arithmetic peaks (one GPU runs): the roofline denominators
+    peaks = measure_alu_peaks(dev.index) if world == 1 else None
 
     u0 = workloads.heat_noise_modes(N_POINTS)
     u0_dev = torch.tensor(u0, device=dev)
@@ -286,61 +436,28 @@ def run_gpu(args):
     e2e_times = []
     for _ in range(max(1, min(args.steps, 3))):
         flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-        torch.cuda.synchronize()
-        e2e_times.append(a.elapsed_time(b) / 1e3)
+        e2e_times.append(cuda_time(e2e_step, stream))
     e2e_value = N_POINTS * NSTEPS * world / statistics.mean(e2e_times)
 
     # stated error: compensated result against the exact Fourier solution
     got = host_out.numpy()
-    k = np.arange(N_POINTS // 2 + 1)
-    exact = np.fft.irfft(np.fft.rfft(u0) * (1.0 - np.sin(np.pi * k / N_POINTS) ** 2) ** NSTEPS,
-                         N_POINTS)
-    max_err = float(np.max(np.abs(got - exact)) / np.max(np.abs(u0)))
+    exact = exact_heat(u0, HEAT_R, NSTEPS)
+    scale = float(np.max(np.abs(u0)))
+    max_err = float(np.max(np.abs(got - exact)) / scale)
 
     # ---- comparison runs (one step each, outside the timed region)
-    def timed(fn):
-        u.copy_(pristine)
+    def timed(fn, dst, src):
+        dst.copy_(src)
         flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / 1e3
+        return cuda_time(fn, stream)
 
-    naive_f32c = N_POINTS * NSTEPS / timed(lambda: sw.swept_naive_advance(plan, u, NSTEPS))
-    plan64 = sw.swept_plan(N_POINTS, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, TILE_B)
-    u64 = u0_dev.clone()
-
-    def timed64(fn):
-        u64.copy_(u0_dev)
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / 1e3
-
-    swept_f64 = N_POINTS * NSTEPS / timed64(lambda: sw.swept_advance(plan64, u64, NSTEPS))
-    naive_f64 = N_POINTS * NSTEPS / timed64(lambda: sw.swept_naive_advance(plan64, u64, NSTEPS))
-    plan64.destroy()
+    naive_f32c = N_POINTS * NSTEPS / timed(lambda: sw.swept_naive_advance(plan, u, NSTEPS), u, pristine)
 
     # plain binary32 state (diagnostic precision): rate and error against the exact solution
     plan32 = sw.swept_plan(N_POINTS, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32, TILE_B)
     u32p = u0_dev.float()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flush.fill_(1)
-    a.record(stream)
-    sw.swept_advance(plan32, u32p, NSTEPS)
-    b.record(stream)
-    torch.cuda.synchronize()
-    swept_f32 = N_POINTS * NSTEPS / (a.elapsed_time(b) / 1e3)
-    err_f32 = float(np.max(np.abs(u32p.double().cpu().numpy() - exact)) / np.max(np.abs(u0)))
+    swept_f32 = N_POINTS * NSTEPS / timed(lambda: sw.swept_advance(plan32, u32p, NSTEPS), u32p, u0_dev.float())
+    err_f32 = float(np.max(np.abs(u32p.double().cpu().numpy() - exact)) / scale)
     plan32.destroy()
     del u32p
 
@@ -348,7 +465,7 @@ def run_gpu(args):
     sweep = {}
     for tb in (64, 128, 256, 512, 1024):
         pb = sw.swept_plan(N_POINTS, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, tb)
-        sweep[str(tb)] = N_POINTS * NSTEPS / timed(lambda: sw.swept_advance(pb, u, NSTEPS))
+        sweep[str(tb)] = N_POINTS * NSTEPS / timed(lambda: sw.swept_advance(pb, u, NSTEPS), u, pristine)
         pb.destroy()
 
     # FP64 reductions of the compensated state (sum, half sum of squares; dot with an FP64
@@ -359,12 +476,8 @@ def run_gpu(args):
         ts = []
         for _ in range(5):
             flush.fill_(1)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            sw.swept_reduce(plan, u, what, v=u0_dev if what == sw.SWEPT_DOT else None)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b) / 1e3)
+            ts.append(cuda_time(lambda: sw.swept_reduce(plan, u, what, v=u0_dev if what == sw.SWEPT_DOT else None),
+                                stream))
         red[name] = {"bytes": nbytes, "ms": statistics.median(ts) * 1e3,
                      "GB/s": nbytes / statistics.median(ts) / 1e9}
 
@@ -373,34 +486,41 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = measured_hbm_gbs()
     # Dominant kernel: the streamed ring kernel (heat, compensated FP32, K = 32), one
     # launch per step running the q - 1 = 38 full-diamond stages (N x h updates each);
     # the other three launches are the first triangle, the last fill and the remainder.
     # Its duration comes from the library's events around it in every timed step.
     n_all, n_ring = launches[0]
     q = NSTEPS // h
-    per_launch_ops = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * h * (q - 1) / n_ring
+    ring_updates = N_POINTS * h * (q - 1) / n_ring
     avg_launch_s = statistics.mean(ring_ms) / 1e3 / n_ring
-    peak_ops = 152 * 128 * sm_max * 1e6
-    achieved = per_launch_ops / avg_launch_s
-    whole = OPS_PER_UPDATE_F32C_HEAT * N_POINTS * NSTEPS / (t_dev / args.steps)
-    roof = {"bound": "alu", "kernel": "swept_stream_kernel<heat,f32c,K=32>",
-            "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops, "traffic": STREAM_K32_TRAFFIC_BYTES,
-            "traffic_unit": "DRAM bytes per launch (ncu)",
-            "algorithmic_edge_bytes_per_launch": 2 * 16 * N_POINTS * (q - 1) / n_ring,
-            "per_launch_ops": per_launch_ops, "avg_launch_ms": avg_launch_s * 1e3,
-            "launches_per_step": n_all, "ring_launches_per_step": n_ring,
-            "achieved_whole_advance": whole / 1e12, "frac_whole_advance": whole / peak_ops,
-            "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, MEASURED_PEAKS.json)"}
-    cpu = time_oracle() if world == 1 else None
+    peak, unit, source, nominal = peak_block(peaks, "fp32")
+    traffic, traffic_note = profile_traffic()
+    roof = roofline(ALGO_OPS_F32C["heat"] * ring_updates / avg_launch_s, peak, unit, source,
+                    kernel="swept_stream_kernel<heat,f32c,K=32>",
+                    traffic=traffic, traffic_unit="DRAM bytes per launch (ncu)", traffic_note=traffic_note,
+                    algorithmic_edge_bytes_per_launch=2 * 16 * N_POINTS * (q - 1) / n_ring,
+                    ops_per_update=ALGO_OPS_F32C["heat"], executed_ops_per_update=EXEC_OPS_F32C["heat"],
+                    per_launch_ops=ALGO_OPS_F32C["heat"] * ring_updates, avg_launch_ms=avg_launch_s * 1e3,
+                    launches_per_step=n_all, ring_launches_per_step=n_ring,
+                    frac_whole_advance=ALGO_OPS_F32C["heat"] * value / world / peak if peak else None,
+                    frac_executed=EXEC_OPS_F32C["heat"] * ring_updates / avg_launch_s / peak if peak else None,
+                    frac_of_nominal=ALGO_OPS_F32C["heat"] * ring_updates / avg_launch_s / nominal)
+    cpu, bitexact = None, None
+    reports = None
+    if world == 1:
+        cpu, steps_s, (ohi, olo) = time_oracle()
+        # the GPU path on the oracle's sample: bit for bit
+        u.copy_(pristine)
+        sw.swept_advance(plan, u, steps_s)
+        gh = u.cpu().numpy()
+        bitexact = bool(np.array_equal(gh[:N_POINTS], ohi) and np.array_equal(gh[N_POINTS:], olo))
+        cpu["gpu_bit_exact_on_sample"] = bitexact
+        plan.destroy()
+        del u, pristine, host_in, host_out, dev64
+        torch.cuda.empty_cache()
+        reports = run_reports(peaks, dev, flush)
     naive_roof = hbm * 1e9 / 16.0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
@@ -412,14 +532,14 @@ def run_gpu(args):
             "gpu_launches": sum(n for n, _ in launches),
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "max_err_vs_exact": max_err,
-            "compare": {"naive_f32c": naive_f32c, "swept_f64": swept_f64, "naive_f64": naive_f64,
-                        "swept_f32_plain": swept_f32, "max_err_f32_plain_vs_exact": err_f32,
+            "compare": {"naive_f32c": naive_f32c, "swept_f32_plain": swept_f32,
+                        "max_err_f32_plain_vs_exact": err_f32,
                         "naive_hbm_roof_16B": naive_roof, "swept_over_naive_hbm_roof": value / world / naive_roof,
                         "swept_over_naive_f32c": value / world / naive_f32c,
-                        "ops_per_update": {"f32c_heat": OPS_PER_UPDATE_F32C_HEAT, "f64_heat": OPS_PER_UPDATE_F64_HEAT},
                         "tile_sweep_f32c": sweep,
                         "reductions_f64": {k: dict(v, frac_of_measured_hbm=v["GB/s"] / hbm)
                                            for k, v in red.items()}},
+            "peaks": peaks, "reports": reports,
             "wall_s": wall}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -427,7 +547,412 @@ def run_gpu(args):
     return 0
 
 
-# ------------------------------------------------- other workloads (reports)
+# ---------------------------------------------------------------- reports
+def run_reports(peaks, dev, flush) -> dict:
+    """Every other workload of the benchmark suite on this GPU, each with its error, its
+    dominant kernel's time and its fraction of the measured peak (one GPU runs only)."""
+    import torch
+    out = {}
+    for name, fn in (("heat_c1_f64", report_heat_f64), ("latency_c0", report_latency_c0),
+                     ("ks_c2", report_ks_c2), ("batch_c3", report_batch_c3),
+                     ("adjoint_c4", report_adjoint_c4)):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(peaks, flush)
+        except Exception as e:        # one report's failure must not hide the others
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    return out
+
+
+def report_heat_f64(peaks, flush):
+    """The headline field (heat, N = 2^24, 20000 steps) in FP64: swept (streamed ring) and naive."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    u0 = workloads.heat_noise_modes(N_POINTS)
+    u0_dev = torch.tensor(u0, device="cuda")
+    u = u0_dev.clone()
+    plan = sw.swept_plan(N_POINTS, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, TILE_B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_TIME_RING, 1)
+
+    def run(fn):
+        u.copy_(u0_dev)
+        flush.fill_(1)
+        return cuda_time(fn)
+
+    run(lambda: sw.swept_advance(plan, u, 2 * plan.h + 1))            # warm-up
+    t_sw = run(lambda: sw.swept_advance(plan, u, NSTEPS))
+    n_all, n_ring, ring_ms = sw.swept_plan_last_advance(plan)
+    err = float(np.max(np.abs(u.cpu().numpy() - exact_heat(u0, HEAT_R, NSTEPS))) / np.max(np.abs(u0)))
+    t_nv = run(lambda: sw.swept_naive_advance(plan, u, NSTEPS))
+    h = plan.h
+    q = NSTEPS // h
+    plan.destroy()
+    peak, unit, source, _ = peak_block(peaks, "fp64")
+    ring_updates = N_POINTS * h * (q - 1)
+    rate_ring = ring_updates / (ring_ms / 1e3) if ring_ms > 0 else None
+    work = ALGO_FLOP_F64["heat"]
+    return {"workload": "heat1d_periodic_N16777216_r0.25_20000steps_f64_B1024", "unit": UNIT,
+            "swept": N_POINTS * NSTEPS / t_sw, "naive": N_POINTS * NSTEPS / t_nv,
+            "swept_over_naive": t_nv / t_sw, "max_err_vs_exact": err,
+            "error_reference": "exact Fourier solution (mode k scaled by g_k per step), relative to max|u0|",
+            "launches": n_all,
+            "roofline": roofline(work * rate_ring if rate_ring else 0.0, peak, unit, source,
+                                 kernel="swept_stream_kernel<heat,f64,K=32>", avg_launch_ms=ring_ms / max(1, n_ring),
+                                 flop_per_update=work, executed_ops_per_update=EXEC_OPS_F64["heat"],
+                                 naive_frac=work * N_POINTS * NSTEPS / t_nv / peak if peak else None)}
+
+
+def report_latency_c0(peaks, flush):
+    """Heat, N = 1024, r = 1/4, 2000 steps, FP64, B = 32: the latency regime.  Per
+    sub-timestep, the swept stages (graph-replayed) against the naive stepper (graph-replayed),
+    the fit of Eq. 1 over B, and the compensated FP32 state."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    from paper_1504_01380_gb300 import tune
+    n, nsteps = 1024, 2000
+    u0 = workloads.heat_modes(n, 8)
+    u0_dev = torch.tensor(u0, device="cuda")
+    u = u0_dev.clone()
+
+    def per_sub(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            u.copy_(u0_dev)
+            best = min(best, cuda_time(fn))
+        return best / nsteps
+
+    graph = {}
+    for B in (32, 64, 128, 256):
+        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, B)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+        graph[B] = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
+        if B == 32:
+            u.copy_(u0_dev)
+            sw.swept_advance(plan, u, nsteps)
+            got32 = u.cpu().numpy()
+            launches = sw.swept_plan_last_advance(plan)[0]
+            h32 = plan.h
+        plan.destroy()
+    plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, 32)
+    g = torch.cuda.CUDAGraph()
+    u.copy_(u0_dev)
+    with torch.cuda.graph(g):
+        sw.swept_naive_advance(plan, u, nsteps)
+    naive = per_sub(g.replay, reps=3)
+    plan.destroy()
+    # compensated FP32 state
+    c0 = sw.swept_f32c_split(u0_dev)
+    c = c0.clone()
+
+    def per_sub32(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            c.copy_(c0)
+            best = min(best, cuda_time(fn))
+        return best / nsteps
+
+    f32c = {}
+    for B in (32, 64):
+        p = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, B)
+        sw.swept_plan_set(p, sw.SWEPT_OPT_GRAPH, 1)
+        f32c[B] = per_sub32(lambda: sw.swept_advance(p, c, nsteps))
+        p.destroy()
+    p = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, 32)
+    g3 = torch.cuda.CUDAGraph()
+    c.copy_(c0)
+    with torch.cuda.graph(g3):
+        sw.swept_naive_advance(p, c, nsteps)
+    naive32 = per_sub32(g3.replay, reps=3)
+    p.destroy()
+    fit = tune.fit_eq1([(B, t) for B, t in graph.items()])
+    exact = exact_heat(u0, HEAT_R, nsteps)
+    err = float(np.max(np.abs(got32 - exact)) / np.max(np.abs(u0)))
+    oracle_leg = cpu_leg_latency(u0, nsteps, got32)
+    t32 = graph[32]
+    best32 = min(f32c, key=f32c.get)
+    # the launch gap: the naive graph's time per sub-timestep is one kernel boundary plus
+    # 1024 points of work; a stage of h sub-timesteps pays it once
+    return {"workload": "heat1d_N1024_r0.25_2000steps_f64_B32", "unit": "ns per sub-timestep",
+            "swept_graph_ns": t32 * 1e9, "naive_graph_ns": naive * 1e9, "speedup_vs_naive_graph": naive / t32,
+            "swept_graph_ns_by_B": {str(B): t * 1e9 for B, t in graph.items()},
+            "launches": launches,
+            "max_err_vs_closed_form": err,
+            "error_reference": "closed form sum_k g_k^n (a_k sin + b_k cos), relative to max|u0|",
+            "f32c": {"swept_graph_ns_by_B": {str(B): t * 1e9 for B, t in f32c.items()},
+                     "naive_graph_ns": naive32 * 1e9, "speedup_vs_naive_graph": naive32 / f32c[best32]},
+            "eq1_fit": {"s_ns": fit["s"] * 1e9, "tau_ns": fit["tau"] * 1e9, "n_star": fit["n_star"]} if fit else None,
+            "roofline": {"bound": "latency", "achieved": t32 * 1e9, "unit": "ns per sub-timestep",
+                         "peak": naive * 1e9 / h32, "frac": (naive / h32) / t32,
+                         "peak_source": ("measured: one kernel boundary (the graph-replayed naive stepper's "
+                                         "time per sub-timestep) paid once per stage of h = 16 sub-timesteps; "
+                                         "the rest of the time is the per-level dependence chain of one warp")},
+            "cpu_baseline": oracle_leg}
+
+
+def cpu_leg_latency(u0, nsteps, got):
+    """Oracle leg of the latency report: the oracle on the same 1024-point run, timed on the host
+    cores, and the GPU result compared with it bit for bit."""
+    import oracle
+    t0 = time.perf_counter()
+    want = oracle.advance_f64(oracle.HEAT, [HEAT_R], u0, nsteps, 1)
+    el = time.perf_counter() - t0
+    return {"kind": "oracle", "cores": 1, "value": u0.size * nsteps / el, "unit": UNIT,
+            "sample": f"the whole workload, N=1024 x {nsteps} sub-timesteps, one thread",
+            "gpu_bit_exact": bool(np.array_equal(got, want))}
+
+
+def report_ks_c2(peaks, flush):
+    """KS (forward Euler), N = 2^22, dx = 0.5, dt = 0.002, 50000 steps, u0 = 0.1 smooth^10(N(0,1)).
+
+    Compensated FP32 (B = 512, streamed ring) over the full 50000 steps against the naive
+    stepper; FP64 swept and naive over 5000 steps (both FP64-pipe-bound).  Error: the
+    compensated state after 2000 steps against the FP64 oracle (after 50000 steps the chaotic
+    dynamics have amplified rounding differences to the size of the solution); the FP64 GPU
+    state after 2000 steps must equal the oracle's bit for bit.
+    """
+    import torch
+    import paper_1504_01380_gb300 as sw
+    n, nsteps, nshort, nerr, B = 1 << 22, 50000, 5000, 2000, 512
+    prm = [workloads.KS_DT, workloads.KS_DX]
+    u0 = workloads.ks_smoothed(n)
+    u64 = torch.tensor(u0, device="cuda")
+    u32 = sw.swept_f32c_split(u64)
+    u = u32.clone()
+
+    def run(fn, dst, src):
+        dst.copy_(src)
+        flush.fill_(1)
+        return cuda_time(fn)
+
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F32C, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_TIME_RING, 1)
+    run(lambda: sw.swept_advance(plan, u, nerr), u, u32)                      # warm-up
+    f32_2000 = sw.swept_f32c_merge(u).cpu().numpy()
+    t = run(lambda: sw.swept_advance(plan, u, nsteps), u, u32)
+    n_all, n_ring, ring_ms = sw.swept_plan_last_advance(plan)
+    h = plan.h
+    t_nv = run(lambda: sw.swept_naive_advance(plan, u, nshort), u, u32)
+    plan.destroy()
+    v = u64.clone()
+    p64 = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F64, 256)
+    t64 = run(lambda: sw.swept_advance(p64, v, nshort), v, u64)
+    t64n = run(lambda: sw.swept_naive_advance(p64, v, nshort), v, u64)
+    run(lambda: sw.swept_advance(p64, v, nerr), v, u64)
+    f64_2000 = v.cpu().numpy()
+    p64.destroy()
+    leg, want = cpu_leg_ks(u0, prm, nerr)
+    scale = float(np.max(np.abs(want)))
+    q = nsteps // h
+    ring_updates = n * h * (q - 1)
+    peak, unit, source, _ = peak_block(peaks, "fp32")
+    leg["gpu_f64_bit_exact"] = bool(np.array_equal(f64_2000, want))
+    rate = n * nsteps / t
+    return {"workload": f"ks1d_N{n}_dx0.5_dt0.002_{nsteps}steps_f32c_B{B}", "unit": UNIT,
+            "swept": rate, "naive": n * nshort / t_nv, "swept_over_naive": rate / (n * nshort / t_nv),
+            "naive_hbm_roof_16B": measured_hbm_gbs() * 1e9 / 16,
+            "f64": {"swept": n * nshort / t64, "naive": n * nshort / t64n, "steps": nshort},
+            "max_err_f32c_vs_oracle_f64_after_2000": float(np.max(np.abs(f32_2000 - want))) / scale,
+            "error_reference": "FP64 oracle after 2000 steps, relative to its max|u|; bar 1e-5",
+            "launches": n_all,
+            "roofline": roofline(ALGO_OPS_F32C["ks"] * ring_updates / (ring_ms / 1e3), peak, unit, source,
+                                 kernel="swept_stream_kernel<ks,f32c,K=16>", avg_launch_ms=ring_ms / max(1, n_ring),
+                                 ops_per_update=ALGO_OPS_F32C["ks"], executed_ops_per_update=EXEC_OPS_F32C["ks"],
+                                 frac_executed=EXEC_OPS_F32C["ks"] * ring_updates / (ring_ms / 1e3) / peak
+                                 if peak else None,
+                                 frac_whole_advance=ALGO_OPS_F32C["ks"] * rate / peak if peak else None),
+            "cpu_baseline": leg}
+
+
+def cpu_leg_ks(u0, prm, nsteps):
+    """Oracle leg of the KS report: the FP64 oracle over the first 2000 steps of the full field on
+    the host cores (timed), whose result is the error reference."""
+    import oracle
+    threads = cores_used()
+    t0 = time.perf_counter()
+    want = oracle.advance_f64(oracle.KS, prm, u0, nsteps, threads)
+    el = time.perf_counter() - t0
+    return ({"kind": "oracle", "cores": threads, "value": u0.size * nsteps / el, "unit": UNIT,
+             "sample": f"N=2^22, first {nsteps} of 50000 steps, FP64, {el:.1f} s"}, want)
+
+
+def report_batch_c3(peaks, flush):
+    """4096 ragged problems (half heat, half KS), compensated FP32, one persistent launch under a
+    CUDA graph, against the naive batched stepper (one launch per time step over every active
+    problem) and one naive launch sequence per problem (a seeded sample)."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    from paper_1504_01380_gb300 import tune
+    kinds, lengths, steps = workloads.batch_problems()
+    prm = {0: (HEAT_R, 0.0), 1: (workloads.KS_DT, workloads.KS_DX)}
+    problems = [(int(k), int(n), int(s), prm[int(k)]) for k, n, s in zip(kinds, lengths, steps)]
+    choice = tune.tune_batch(problems, sw.SWEPT_F32C)
+    batch = sw.swept_batch_plan(problems, sw.SWEPT_F32C, choice["B_heat"], choice["B_ks"])
+    states = workloads.batch_initial(kinds, lengths)
+    pool = torch.zeros(batch.pool_bytes, dtype=torch.uint8, device="cuda")
+    for off, s0 in zip(batch.offsets, states):
+        seg = pool[off:off + 8 * len(s0)].view(torch.float32)
+        sw.swept_f32c_split(torch.tensor(s0, device="cuda"), out=seg)
+    pristine = pool.clone()
+    work = {0: float(np.sum(np.where(kinds == 0, lengths * steps, 0).astype(np.float64))),
+            1: float(np.sum(np.where(kinds == 1, lengths * steps, 0).astype(np.float64)))}
+    total = work[0] + work[1]
+
+    def run(fn):
+        pool.copy_(pristine)
+        flush.fill_(1)
+        return cuda_time(fn)
+
+    run(lambda: sw.swept_advance_batch(batch, pool))                          # warm-up (graph capture)
+    times = [run(lambda: sw.swept_advance_batch(batch, pool)) for _ in range(2)]
+    status = sw.swept_batch_status(batch)
+    t = min(times)
+    result = pool.clone()
+    t_nb = run(lambda: sw.swept_batch_naive_advance(batch, pool))             # allocates on first use
+    t_nb = run(lambda: sw.swept_batch_naive_advance(batch, pool))
+    # one naive launch sequence per problem, a seeded sample of 16
+    rng = np.random.default_rng(1)
+    sample = rng.choice(len(problems), 16, replace=False)
+    nu, ns = 0.0, 0.0
+    for i in sample:
+        st, n, nst, p = problems[i]
+        plan = sw.swept_plan(n, sw.RADIUS[st], st, p[: 1 if st == 0 else 2], sw.SWEPT_F32C, 0)
+        uu = sw.swept_f32c_split(torch.tensor(states[i], device="cuda"))
+        ns += cuda_time(lambda: sw.swept_naive_advance(plan, uu, nst))
+        nu += n * nst
+        plan.destroy()
+    # oracle leg: a seeded sample of small problems, bit for bit, and the compensated state's error
+    leg = cpu_leg_batch(problems, states, batch.offsets, result.cpu().numpy())
+    info = batch.info()
+    batch.destroy()
+    peak, unit, source, _ = peak_block(peaks, "fp32")
+    ops = ALGO_OPS_F32C["heat"] * work[0] + ALGO_OPS_F32C["ks"] * work[1]
+    exe = EXEC_OPS_F32C["heat"] * work[0] + EXEC_OPS_F32C["ks"] * work[1]
+    return {"workload": "batch_4096_ragged_heat_ks_f32c", "unit": UNIT, "problems": len(problems),
+            "sum_N_x_steps": total, "swept": total / t, "status": status,
+            "naive_batched": total / t_nb, "swept_over_naive_batched": t_nb / t,
+            "naive_per_problem": {"value": nu / ns, "sample": "16 seeded problems, one launch per sub-timestep"},
+            "B_heat": choice["B_heat"], "B_ks": choice["B_ks"], "tuning": choice["rates"], **info,
+            "roofline": roofline(ops / t, peak, unit, source, kernel="swept_batch_kernel (one launch)",
+                                 avg_launch_ms=t * 1e3, ops_per_update={"heat": 11, "ks": 22},
+                                 frac_executed=exe / t / peak if peak else None),
+            "cpu_baseline": leg}
+
+
+def cpu_leg_batch(problems, states, offsets, pool_bytes: np.ndarray, count: int = 12):
+    """Oracle leg of the batch report: a seeded sample of problems with at most 2e8 cell-updates,
+    each stepped by the compensated oracle (one thread, timed) and compared bit for bit with the
+    GPU batch result; the compensated result's error against the FP64 oracle (heat at the final
+    step; KS over at most 2000 steps is covered by the KS report)."""
+    import oracle
+    small = [i for i, (_, n, s, _) in enumerate(problems) if n * s <= 2e8]
+    rng = np.random.default_rng(7)
+    pick = sorted(rng.choice(small, min(count, len(small)), replace=False).tolist())
+    exact, worst, el, upd = True, 0.0, 0.0, 0.0
+    for i in pick:
+        st, n, nst, p = problems[i]
+        prm = list(p[: 1 if st == 0 else 2])
+        hi, lo = oracle.split_f32c(states[i])
+        t0 = time.perf_counter()
+        whi, wlo = oracle.advance_f32c(st, prm, hi, lo, nst, 1)
+        el += time.perf_counter() - t0
+        upd += n * nst
+        seg = pool_bytes[offsets[i]:offsets[i] + 8 * n].view(np.float32)
+        exact = exact and np.array_equal(seg[:n], whi) and np.array_equal(seg[n:], wlo)
+        if st == 0:
+            w64 = oracle.advance_f64(st, prm, states[i], nst, 1)
+            got = seg[:n].astype(np.float64) + seg[n:].astype(np.float64)
+            worst = max(worst, float(np.max(np.abs(got - w64)) / np.max(np.abs(states[i]))))
+    return {"kind": "oracle", "cores": 1, "value": upd / el, "unit": UNIT,
+            "sample": f"{len(pick)} seeded problems of at most 2e8 cell-updates, one thread each",
+            "gpu_bit_exact": bool(exact), "max_err_heat_f32c_vs_oracle_f64": worst}
+
+
+def report_adjoint_c4(peaks, flush):
+    """Gradient of J = 1/2 sum u(T)^2 for KS, N = 2^20, 20000 steps, FP64, B = 256, checkpoint
+    interval at most 64 cycles; checked against central finite differences (eps = 1e-6) along
+    32 seeded directions and against the oracle's discrete adjoint at N = 256, 500 steps."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    n, nsteps, K, eps = 1 << 20, 20000, 64, 1e-6
+    prm = [workloads.KS_DT, workloads.KS_DX]
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F64, 256)
+    u0 = torch.tensor(workloads.ks_adjoint_state(n), device="cuda")
+    uT = u0.clone()
+    t_fwd = cuda_time(lambda: sw.swept_advance(plan, uT, nsteps))
+    g = torch.empty_like(u0)
+    sw.swept_adjoint(plan, u0, uT, nsteps, K, out=g)                       # warm-up (allocates)
+    torch.cuda.synchronize()
+    t_grad = cuda_time(lambda: sw.swept_adjoint(plan, u0, uT, nsteps, K, out=g))
+    scratch = sw.swept_adjoint_scratch(plan, nsteps, K) if "swept_adjoint_scratch" in dir(sw) else None
+    w = torch.empty_like(u0)
+    jbuf = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def J(x):
+        w.copy_(x)
+        sw.swept_advance(plan, w, nsteps)
+        sw.swept_reduce(plan, w, sw.SWEPT_HALF_SUMSQ, out=jbuf)
+        return float(jbuf.item())
+
+    rel, conv = [], []
+    t0 = time.perf_counter()
+    for d in range(32):
+        v = torch.tensor(workloads.fd_direction(n, d), device="cuda")
+        sw.swept_reduce(plan, g, sw.SWEPT_DOT, v=v, out=jbuf)
+        ad = float(jbuf.item())
+        fd = (J(u0 + eps * v) - J(u0 - eps * v)) / (2 * eps)
+        rel.append(abs(fd - ad) / abs(ad))
+        if d < 4:                 # convergence in eps: the O(eps^2) truncation shrinks 4x per halving
+            fd2 = (J(u0 + 0.5 * eps * v) - J(u0 - 0.5 * eps * v)) / eps
+            conv.append(abs(fd - ad) / max(abs(fd2 - ad), 1e-300))
+    t_fd = time.perf_counter() - t0
+    plan.destroy()
+    small = cpu_leg_adjoint()
+    peak, unit, source, _ = peak_block(peaks, "fp64")
+    flop = 3 * ALGO_FLOP_F64["ks"] * n * nsteps
+    return {"workload": "ks_adjoint_N1048576_20000steps_f64_B256_K64", "unit": "s per gradient",
+            "gradient_s": t_grad, "forward_s": t_fwd, "gradient_over_forward": t_grad / t_fwd,
+            "forward_equivalent_rate": n * nsteps / t_grad, "scratch_bytes": scratch,
+            "fd": {"directions": 32, "eps": eps, "rel_err_max": max(rel), "rel_err_median": statistics.median(rel),
+                   "under_1e-6": sum(r < 1e-6 for r in rel),
+                   "error_ratio_eps_over_half_eps": conv, "wall_s": t_fd,
+                   "reading": ("over 20000 chaotic steps the central difference's O(eps^2) truncation "
+                               "is amplified past 1e-6; the ratio near 4 per halving of eps shows "
+                               "the difference converging to the adjoint")},
+            "roofline": roofline(flop / t_grad, peak, unit, source,
+                                 kernel="gradient: forward with checkpoints + tape recompute + transposed sweep",
+                                 flop_per_cell_step=3 * ALGO_FLOP_F64["ks"]),
+            "oracle_check": small}
+
+
+def cpu_leg_adjoint():
+    """Oracle leg of the adjoint report: the oracle's discrete adjoint at N = 256, 500 steps
+    against the GPU's, bit for bit and in relative max-norm (bar 1e-12)."""
+    import torch
+    import oracle
+    import paper_1504_01380_gb300 as sw
+    n, nsteps = 256, 500
+    prm = [workloads.KS_DT, workloads.KS_DX]
+    u0 = workloads.ks_smoothed(n, 11) * 10.0
+    uT = oracle.advance_f64(oracle.KS, prm, u0, nsteps)
+    t0 = time.perf_counter()
+    want = oracle.adjoint_f64(oracle.KS, prm, u0, uT, nsteps)
+    el = time.perf_counter() - t0
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F64, 64)
+    got = sw.swept_adjoint(plan, torch.tensor(u0, device="cuda"), torch.tensor(uT, device="cuda"),
+                           nsteps, 64).cpu().numpy()
+    plan.destroy()
+    return {"kind": "oracle", "cores": 1, "value": n * nsteps / el, "unit": "cell-steps/s of the discrete adjoint",
+            "sample": "N=256, 500 steps", "gpu_bit_exact": bool(np.array_equal(got, want)),
+            "rel_max_diff": float(np.max(np.abs(got - want)) / np.max(np.abs(want)))}
+
+
+# ------------------------------------------------- other workloads (lines)
 def shard_problems(work, world: int):
     """Split independent problems over ranks: greedy longest-first on N*steps.
 
@@ -456,7 +981,8 @@ def max_over_ranks(t: float, world: int, device=None) -> float:
 
 
 def run_batch_workload(args):
-    """4096 ragged problems (half heat, half KS), compensated FP32, one persistent launch."""
+    """4096 ragged problems (half heat, half KS), compensated FP32, one persistent launch per rank
+    (the problems sharded over ranks, no exchange)."""
     import torch
     import paper_1504_01380_gb300 as sw
     from paper_1504_01380_gb300 import tune
@@ -474,15 +1000,12 @@ def run_batch_workload(args):
     choice = tune.tune_batch(problems, sw.SWEPT_F32C)
     batch = sw.swept_batch_plan(problems, sw.SWEPT_F32C, choice["B_heat"], choice["B_ks"])
     states = workloads.batch_initial(kinds, lengths, seed_offsets=mine)
-    host = np.zeros(batch.pool_bytes, dtype=np.uint8)
-    pool = torch.tensor(host, device="cuda")
+    pool = torch.zeros(batch.pool_bytes, dtype=torch.uint8, device="cuda")
     for off, u0 in zip(batch.offsets, states):
-        t = torch.tensor(u0, device="cuda")
         seg = pool[off:off + 8 * len(u0)].view(torch.float32)
-        sw.swept_f32c_split(t, out=seg)
+        sw.swept_f32c_split(torch.tensor(u0, device="cuda"), out=seg)
     pristine = pool.clone()
     total = float(np.sum(lengths.astype(np.float64) * steps))
-    total_local = total
     for _ in range(args.warmup):
         pool.copy_(pristine)
         sw.swept_advance_batch(batch, pool)
@@ -490,44 +1013,13 @@ def run_batch_workload(args):
     ms = []
     for _ in range(args.steps):
         pool.copy_(pristine)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        sw.swept_advance_batch(batch, pool)
-        b.record()
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
+        ms.append(cuda_time(lambda: sw.swept_advance_batch(batch, pool)) * 1e3)
     status = sw.swept_batch_status(batch)
     t = max_over_ranks(sum(ms) / 1e3 / args.steps, world, torch.device("cuda", torch.cuda.current_device()))
     if world > 1:
         tot = torch.tensor([total], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(tot)
         total = float(tot.item())
-    # baseline: one naive launch sequence per problem, on a seeded sample of 64 problems
-    rng = np.random.default_rng(1)
-    sample = rng.choice(len(problems), 64, replace=False)
-    naive_updates, naive_s = 0.0, 0.0
-    for i in sample:
-        st, n, ns, p = problems[i]
-        plan = sw.swept_plan(n, sw.RADIUS[st], st, p[: 1 if st == 0 else 2], sw.SWEPT_F32C, 0)
-        u = sw.swept_f32c_split(torch.tensor(states[i], device="cuda"))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        sw.swept_naive_advance(plan, u, ns)
-        b.record()
-        torch.cuda.synchronize()
-        naive_s += a.elapsed_time(b) / 1e3
-        naive_updates += n * ns
-        plan.destroy()
-    # stronger baseline: one launch per time step over every problem still active
-    pool.copy_(pristine)
-    sw.swept_batch_naive_advance(batch, pool)          # warm-up (allocates the scratch pool)
-    pool.copy_(pristine)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    sw.swept_batch_naive_advance(batch, pool)
-    b.record()
-    torch.cuda.synchronize()
-    naive_batched = total_local / (a.elapsed_time(b) / 1e3)
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": total / t, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -536,110 +1028,21 @@ def run_batch_workload(args):
             "config": {"workload": "batch_4096_ragged_heat_ks_f32c", "problems": len(problems),
                        "sum_N_x_steps": total, "B_heat": choice["B_heat"], "B_ks": choice["B_ks"],
                        "tuning": choice["rates"], **batch.info()},
-            "status": status,
-            "baseline_naive_per_problem": {"value": naive_updates / naive_s, "unit": UNIT,
-                                           "sample": "64 seeded problems, one launch per sub-timestep"},
-            "baseline_naive_batched": {"value": naive_batched, "unit": UNIT,
-                                       "what": "one launch per time step over every active problem, rank 0"}}
+            "status": status}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_adjoint_workload(args):
-    """Gradient of J = 1/2 sum u(T)^2 for KS N = 2^20, 20000 steps, FP64, checkpoints every 64 cycles."""
+def _report_line(name, fn, args):
+    """Print one report as its own line (peaks measured first)."""
     import torch
     import paper_1504_01380_gb300 as sw
-    n, nsteps = 1 << 20, 20000
-    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, [workloads.KS_DT, workloads.KS_DX], sw.SWEPT_F64, 256)
-    u0 = torch.tensor(workloads.ks_adjoint_state(n), device="cuda")
-    uT = u0.clone()
-    sw.swept_advance(plan, uT, nsteps)
-    ms = []
-    for i in range(args.warmup + args.steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        sw.swept_adjoint(plan, u0, uT, nsteps, 64)
-        b.record()
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            ms.append(a.elapsed_time(b))
-    t = sum(ms) / 1e3 / args.steps
-    f = u0.clone()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    sw.swept_advance(plan, f, nsteps)
-    b.record()
-    torch.cuda.synchronize()
-    fwd = a.elapsed_time(b) / 1e3
-    line = {"metric": METRIC, "value": n * nsteps / t, "unit": UNIT + " (forward-equivalent, gradient)",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
-            "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ks_adjoint_N1048576_20000steps_f64_B256_K64"},
-            "forward_only": {"value": n * nsteps / fwd, "unit": UNIT}}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_ks_workload(args):
-    """KS (forward Euler), N = 2^22, dx = 0.5, dt = 0.002, 50000 steps, u0 = 0.1 smooth^10(N(0,1)).
-
-    Compensated FP32: swept over B in {256, 512, 1024} for the full 50000 steps, against the
-    naive stepper (5000 steps, steady rate).  FP64: swept and naive over 5000 steps (both
-    FP64-pipe-bound).  Error of the compensated state: max-norm difference from the FP64
-    swept path (which the tests hold bit-exact to the oracle) after 2000 steps, relative to
-    max|u|; after 50000 steps the chaotic dynamics have amplified rounding differences to the
-    size of the solution, so that figure is reported only as the divergence time scale.
-    """
-    import torch
-    import paper_1504_01380_gb300 as sw
-    n, nsteps, nshort, nerr = 1 << 22, 50000, 5000, 2000
-    prm = [workloads.KS_DT, workloads.KS_DX]
-    u64 = torch.tensor(workloads.ks_smoothed(n), device="cuda")
-    u32 = sw.swept_f32c_split(u64)
-
-    def timed(fn, u, u0):
-        u.copy_(u0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        fn()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / 1e3
-
-    res = {}
-    u = u32.clone()
-    for B in (256, 512, 1024):
-        plan = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F32C, B)
-        timed(lambda: sw.swept_advance(plan, u, nerr), u, u32)            # warm-up
-        res[str(B)] = n * nsteps / timed(lambda: sw.swept_advance(plan, u, nsteps), u, u32)
-        plan.destroy()
-    best = max(res, key=res.get)
-    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F32C, int(best))
-    naive32 = n * nshort / timed(lambda: sw.swept_naive_advance(plan, u, nshort), u, u32)
-    timed(lambda: sw.swept_advance(plan, u, nerr), u, u32)
-    f32_2000 = sw.swept_f32c_merge(u)
-    timed(lambda: sw.swept_advance(plan, u, nsteps), u, u32)
-    f32_end = sw.swept_f32c_merge(u)
-    plan.destroy()
-    v = u64.clone()
-    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F64, 256)
-    swept64 = n * nshort / timed(lambda: sw.swept_advance(plan, v, nshort), v, u64)
-    naive64 = n * nshort / timed(lambda: sw.swept_naive_advance(plan, v, nshort), v, u64)
-    timed(lambda: sw.swept_advance(plan, v, nerr), v, u64)
-    f64_2000 = v.clone()
-    plan.destroy()
-    scale = float(torch.max(torch.abs(f64_2000)))
-    err2000 = float(torch.max(torch.abs(f32_2000 - f64_2000))) / scale
-    line = {"metric": METRIC, "value": res[best], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": n * nsteps / res[best] * 1e3, "higher_is_better": True, "scaling": "weak",
-            "dtype": "f32c", "data": "synthetic",
-            "config": {"workload": f"ks1d_N{n}_dx0.5_dt0.002_{nsteps}steps_f32c", "B": int(best)},
-            "tile_sweep": res, "naive_f32c": naive32, "swept_f64": swept64, "naive_f64": naive64,
-            "swept_over_naive_f32c": res[best] / naive32,
-            "naive_hbm_roof_16B": measured_hbm_gbs() * 1e9 / 16,
-            "err_f32c_vs_f64_after_2000_steps": err2000,
-            "max_abs_u_after_50000_steps_f32c": float(torch.max(torch.abs(f32_end)))}
-    print(json.dumps(line), flush=True)
+    sw.load()
+    torch.cuda.set_device(0)
+    peaks = measure_alu_peaks(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rep = fn(peaks, flush)
+    print(json.dumps({"report": name, "peaks": peaks, **rep}), flush=True)
     return 0
 
 
@@ -658,22 +1061,12 @@ def run_ks_rk2_workload(args):
         ms = []
         for _ in range(args.steps):
             u.copy_(u0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            sw.swept_advance(plan, u, nsteps)
-            b.record()
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
-        res[str(B)] = n * nsteps / (sum(ms) / 1e3 / args.steps)
+            ms.append(cuda_time(lambda: sw.swept_advance(plan, u, nsteps)))
+        res[str(B)] = n * nsteps / (sum(ms) / args.steps)
         plan.destroy()
     plan = sw.swept_plan(n, 2, sw.SWEPT_KS_RK2, prm, sw.SWEPT_F64, 256)
     u = u0.clone()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    sw.swept_naive_advance(plan, u, nsteps)
-    b.record()
-    torch.cuda.synchronize()
-    naive = n * nsteps / (a.elapsed_time(b) / 1e3)
+    naive = n * nsteps / cuda_time(lambda: sw.swept_naive_advance(plan, u, nsteps))
     best = max(res, key=res.get)
     line = {"metric": METRIC, "value": res[best], "unit": UNIT + " (time steps of 2 sub-timesteps)",
             "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": n * nsteps / res[best] * 1e3,
@@ -684,133 +1077,9 @@ def run_ks_rk2_workload(args):
     return 0
 
 
-def run_latency_workload(args):
-    """The latency regime of Sections 4 and 6: heat, N = 1024, r = 1/4, 2000 steps, FP64.
-
-    The per-step stepper pays one launch (the GPU's latency tau) per
-    sub-timestep; the swept advance pays one per stage of h = B/2 sub-timesteps.
-    Reports the time per sub-timestep for B in {32, ..., 1024} (stages launched
-    directly and replayed as a CUDA graph), for the naive stepper (launched and
-    graph-replayed), and the fit of Eq. 1, t(n) = n s + 2 tau / n with n = B.
-    """
-    import torch
-    import paper_1504_01380_gb300 as sw
-    from paper_1504_01380_gb300 import tune
-    n, nsteps = 1024, 2000
-    u0 = torch.tensor(workloads.heat_modes(n, 8), device="cuda")
-    u = u0.clone()
-
-    def per_sub(fn, reps=5):
-        fn()
-        torch.cuda.synchronize()
-        best = float("inf")
-        for _ in range(reps):
-            u.copy_(u0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            b.record()
-            torch.cuda.synchronize()
-            best = min(best, a.elapsed_time(b) / 1e3)
-        return best / nsteps
-
-    swept, swept_graph = {}, {}
-    for B in (32, 64, 128, 256, 512, 1024):
-        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, B)
-        swept[str(B)] = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
-        sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
-        swept_graph[str(B)] = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
-        plan.destroy()
-    plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, 32)
-    naive = per_sub(lambda: sw.swept_naive_advance(plan, u, nsteps), reps=3)
-    g = torch.cuda.CUDAGraph()
-    u.copy_(u0)
-    with torch.cuda.graph(g):
-        sw.swept_naive_advance(plan, u, nsteps)
-    naive_graph = per_sub(g.replay, reps=3)
-    # the same without programmatic dependent launches (plain kernel boundaries)
-    sw.swept_plan_set(plan, sw.SWEPT_OPT_PDL, 0)
-    g2 = torch.cuda.CUDAGraph()
-    u.copy_(u0)
-    with torch.cuda.graph(g2):
-        sw.swept_naive_advance(plan, u, nsteps)
-    naive_graph_nopdl = per_sub(g2.replay, reps=3)
-    plan.destroy()
-    plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, 32)
-    sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
-    sw.swept_plan_set(plan, sw.SWEPT_OPT_PDL, 0)
-    swept_graph_nopdl = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
-    plan.destroy()
-    # every stage in one persistent launch (device flags instead of kernel boundaries)
-    persistent = {}
-    for B in (32, 64, 128):
-        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, B)
-        sw.swept_plan_set(plan, sw.SWEPT_OPT_PERSISTENT, 1)
-        persistent[str(B)] = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
-        status = sw.swept_plan_status(plan)
-        plan.destroy()
-        if status != 0:
-            persistent[str(B)] = None
-    # the same regime on the compensated FP32 state: per-level work on the FP32 pipe is far
-    # cheaper than on GB300's FP64 pipe, so the launch latency weighs more
-    c0 = sw.swept_f32c_split(u0)
-    c = c0.clone()
-
-    def per_sub32(fn, reps=5):
-        fn()
-        torch.cuda.synchronize()
-        best = float("inf")
-        for _ in range(reps):
-            c.copy_(c0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            b.record()
-            torch.cuda.synchronize()
-            best = min(best, a.elapsed_time(b) / 1e3)
-        return best / nsteps
-
-    f32c = {}
-    for B in (32, 64, 128):
-        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, B)
-        sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
-        f32c[str(B)] = per_sub32(lambda: sw.swept_advance(plan, c, nsteps))
-        plan.destroy()
-    plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, 32)
-    g3 = torch.cuda.CUDAGraph()
-    c.copy_(c0)
-    with torch.cuda.graph(g3):
-        sw.swept_naive_advance(plan, c, nsteps)
-    naive32_graph = per_sub32(g3.replay, reps=3)
-    plan.destroy()
-    best32 = min(f32c, key=f32c.get)
-    fit = tune.fit_eq1([(int(b), t) for b, t in swept_graph.items()])
-    best = min(swept_graph, key=swept_graph.get)
-    line = {"metric": "time per sub-timestep (latency regime)", "value": swept_graph[best] * 1e9,
-            "unit": "ns per sub-timestep", "higher_is_better": False, "n_gpus": 1,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "heat1d_N1024_r0.25_2000steps_f64", "best_B": int(best)},
-            "swept_ns": {b: t * 1e9 for b, t in swept.items()},
-            "swept_graph_ns": {b: t * 1e9 for b, t in swept_graph.items()},
-            "naive_ns": naive * 1e9, "naive_graph_ns": naive_graph * 1e9,
-            "without_pdl": {"swept_graph_ns_B32": swept_graph_nopdl * 1e9, "naive_graph_ns": naive_graph_nopdl * 1e9},
-            "swept_persistent_ns": {b: (t * 1e9 if t is not None else None) for b, t in persistent.items()},
-            "speedup_vs_naive": naive / swept_graph[best],
-            "speedup_vs_naive_graph": naive_graph / swept_graph[best],
-            "f32c": {"workload": "heat1d_N1024_r0.25_2000steps_f32c", "best_B": int(best32),
-                     "swept_graph_ns": {b: t * 1e9 for b, t in f32c.items()},
-                     "naive_graph_ns": naive32_graph * 1e9,
-                     "speedup_vs_naive_graph": naive32_graph / f32c[best32]},
-            "eq1_fit": {"s_ns": fit["s"] * 1e9, "tau_ns": fit["tau"] * 1e9,
-                        "n_star": fit["n_star"]} if fit else None}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
 def euler_state(n: int, cfl: float = 0.2):
     """Periodic Sod state of Section 7 (rho, u, p = 0.125, 0, 0.1 | 1, 0, 1) on [0, 1), gamma 1.4,
     as planar rho/m/E; dt = cfl * dx."""
-    import numpy as np
     x = (np.arange(n) + 0.5) / n
     left = x < 0.5
     rho = np.where(left, 0.125, 1.0)
@@ -845,12 +1114,7 @@ def run_euler_workload(args):
             ts = []
             for _ in range(reps):
                 u.copy_(u0)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                fn()
-                b.record()
-                torch.cuda.synchronize()
-                ts.append(a.elapsed_time(b) / 1e3)
+                ts.append(cuda_time(fn))
             return sum(ts) / len(ts)
 
         res = {}
@@ -905,21 +1169,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="heat",
-                    choices=["heat", "ks", "batch", "adjoint", "ks_rk2", "latency", "euler"],
-                    help="heat: the headline; the others print report lines for those workloads")
+                    choices=["heat", "ks", "batch", "adjoint", "latency", "heat_f64", "ks_rk2", "euler"],
+                    help="heat: the headline line (with every report on one GPU); the others print one "
+                         "line for that workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch_workload(args)
-    if args.workload == "adjoint":
-        return run_adjoint_workload(args)
-    if args.workload == "ks":
-        return run_ks_workload(args)
+    reports = {"ks": ("ks_c2", report_ks_c2), "adjoint": ("adjoint_c4", report_adjoint_c4),
+               "latency": ("latency_c0", report_latency_c0), "heat_f64": ("heat_c1_f64", report_heat_f64)}
+    if args.workload in reports:
+        return _report_line(*reports[args.workload], args)
     if args.workload == "ks_rk2":
         return run_ks_rk2_workload(args)
-    if args.workload == "latency":
-        return run_latency_workload(args)
     if args.workload == "euler":
         return run_euler_workload(args)
     return run_gpu(args)

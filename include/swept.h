@@ -12,7 +12,11 @@
  *   - Return value: SWEPT_OK (0) or a negative SWEPT_E* code; nothing is
  *     thrown or aborted across the ABI.  swept_strerror() names a code.
  *   - Pointers documented as "device" must point to memory of the current
- *     CUDA device, 16-byte aligned; the caller owns them.
+ *     CUDA device (or managed memory), 16-byte aligned; the caller owns
+ *     them.  A plan or batch is used on the device it was made on, with a
+ *     stream of that device.  Each entry point checks this before it
+ *     enqueues anything and returns SWEPT_EINVAL otherwise (a kernel given
+ *     another GPU's pointer would fault).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls enqueue work on it and return without synchronising
  *     unless stated otherwise.
@@ -411,22 +415,63 @@ void swept_batch_destroy(swept_batch_t batch);
  * memory declared inside the library (32 * SWEPT_NOALLOC_MAX_N bytes =
  * 32 MiB); every GPU that loads the library holds that array until the
  * process exits.
- *   N, stencil_id, params, nparams, dtype, B: as swept_plan (B must be given;
- *           radius is implied by the stencil).  N <= SWEPT_NOALLOC_MAX_N,
- *           else SWEPT_ETOOBIG.
- *   u       device state, overwritten with u(nsteps), as swept_advance.
+ *   stencil_id  SWEPT_HEAT (params {r}) or SWEPT_KS (params {dt, dx});
+ *               any other stencil: SWEPT_EINVAL.  The radius is implied.
+ *   dtype       SWEPT_F64 or SWEPT_F32C; SWEPT_F32 or another value:
+ *               SWEPT_EINVAL.
+ *   B           must be given: 32*K with K in {1,2,4,8,16,32} (other
+ *               multiples of 32: SWEPT_ENOTSUP; not a positive multiple of
+ *               32, or K not a multiple of the radius: SWEPT_EINVAL).
+ *   N           a positive multiple of B (the plan's uneven tiles are not
+ *               taken here: N % B != 0 gives SWEPT_EINVAL), at most
+ *               SWEPT_NOALLOC_MAX_N, else SWEPT_ETOOBIG.
+ *   u       device state of the current device, 16-byte aligned, overwritten
+ *           with u(nsteps), as swept_advance; u or the stream on another
+ *           device: SWEPT_EINVAL.
+ *   nsteps  >= 0 sub-timesteps; 0 is a no-op.
  * Results are identical to swept_advance with the same arguments.
  * All calls share the one array: calls that overlap on the GPU (different
  * streams or host threads without ordering) race and corrupt each other.
  * Nothing in the array needs to start at zero (each stage writes the edges
  * the next stage reads).  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress, with that device current) and caches
- * it; make that first call before any stream capture.
+ * it; make that first call before any stream capture.  The cached address
+ * lasts as long as the process: after cudaDeviceReset (or anything else that
+ * destroys the device's primary context) unload and reload the library
+ * before calling it again on that device.
  * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP, SWEPT_ETOOBIG, SWEPT_ECUDA.
  */
 #define SWEPT_NOALLOC_MAX_N (1 << 20)
 int swept_advance_noalloc(int64_t N, int stencil_id, const double *params, int nparams,
                           int dtype, int B, void *u, int64_t nsteps, void *stream);
+
+/* ---- measured peaks ---------------------------------------------------- */
+
+/*
+ * swept_probe_alu -- measure this GPU's peak arithmetic rate, the roofline
+ * denominator of the swept kernels (they are bound by the FP32 pipe for the
+ * compensated state and by the FP64 pipe for FP64, not by memory).  Section 4
+ * models a node by its speed as a given constant; this measures it.  Enqueues
+ * one kernel on `stream` whose blocks fill every SM at full residency; each
+ * thread runs independent dependency chains of the chosen operation, so the
+ * launch time is set by the pipe's throughput.  Time the launch with events
+ * on the same stream: rate = *ops / seconds.  Nothing is allocated or written
+ * (the chains' sum goes to an internal array only if it reaches a value it
+ * never reaches).
+ *   kind   SWEPT_PROBE_F32_ADD, SWEPT_PROBE_F32_FMA, SWEPT_PROBE_F64_ADD or
+ *          SWEPT_PROBE_F64_FMA.
+ *   iters  loop trips per thread, 1 .. 2^40 (each trip is 64 operations per
+ *          thread; about 2e5 trips make an FP32 launch of a few milliseconds).
+ *   ops    host double: the operations the launch performs (an add or an fma
+ *          counts as one).
+ * Errors: SWEPT_EINVAL (kind, iters, null ops, a stream of another device),
+ * SWEPT_ECUDA.
+ */
+#define SWEPT_PROBE_F32_ADD 0
+#define SWEPT_PROBE_F32_FMA 1
+#define SWEPT_PROBE_F64_ADD 2
+#define SWEPT_PROBE_F64_FMA 3
+int swept_probe_alu(int kind, int64_t iters, double *ops, void *stream);
 
 /* ---- diagnostics ------------------------------------------------------ */
 

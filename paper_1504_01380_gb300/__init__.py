@@ -24,6 +24,7 @@ SWEPT_NOALLOC_MAX_N = 1 << 20
 SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS, SWEPT_OPT_GRAPH, SWEPT_OPT_PDL, SWEPT_OPT_PERSISTENT = 0, 1, 2, 3, 4
 SWEPT_OPT_DROP_WINDOW, SWEPT_OPT_TIMEOUT_MS, SWEPT_OPT_STREAM, SWEPT_OPT_TIME_RING = 5, 6, 7, 8
 SWEPT_DIAMOND_AUTO, SWEPT_DIAMOND_WINDOW, SWEPT_DIAMOND_RING = 0, 1, 2
+SWEPT_PROBE_F32_ADD, SWEPT_PROBE_F32_FMA, SWEPT_PROBE_F64_ADD, SWEPT_PROBE_F64_FMA = 0, 1, 2, 3
 
 RADIUS = {SWEPT_HEAT: 1, SWEPT_KS: 2, SWEPT_HEAT_RK2: 1, SWEPT_KS_RK2: 2, SWEPT_EULER: 1}
 
@@ -34,7 +35,7 @@ EXPORTS = (
     "swept_advance_noalloc", "swept_plan_set",
     "swept_batch_plan", "swept_batch_set", "swept_batch_info", "swept_advance_batch",
     "swept_batch_status", "swept_batch_destroy", "swept_adjoint", "swept_batch_naive_advance",
-    "swept_plan_status", "swept_plan_last_advance",
+    "swept_plan_status", "swept_plan_last_advance", "swept_probe_alu",
 )
 
 SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH, SWEPT_BOPT_RUN_LEN = 0, 1, 2, 3, 4
@@ -109,6 +110,8 @@ def load(path: str | None = None):
         L.swept_batch_destroy.restype = None
         L.swept_adjoint.argtypes = [vp, vp, vp, vp, i64, i32, vp]
         L.swept_adjoint.restype = i32
+        L.swept_probe_alu.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), vp]
+        L.swept_probe_alu.restype = i32
         L.swept_strerror.argtypes = [i32]
         L.swept_strerror.restype = ctypes.c_char_p
         L.swept_version.argtypes = []
@@ -143,6 +146,9 @@ def _dev_ptr(t, nbytes: int, what: str):
         raise TypeError(f"{what}: expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{what}: tensor must be contiguous")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{what}: tensor is on {t.device}, but the current device is "
+                         f"cuda:{torch.cuda.current_device()} (the library runs every call there)")
     if t.numel() * t.element_size() < nbytes:
         raise ValueError(f"{what}: tensor holds {t.numel() * t.element_size()} bytes, needs {nbytes}")
     return ctypes.c_void_p(t.data_ptr())
@@ -265,6 +271,15 @@ def swept_reduce(plan: Plan, u, what: int, v=None, out=None, stream=None):
                                int(what), vp,
                                _dev_ptr(out, 8, "out"), _stream(stream)), "swept_reduce")
     return out
+
+
+def swept_probe_alu(kind: int, iters: int, stream=None) -> float:
+    """Enqueue the peak-rate probe (SWEPT_PROBE_*) on ``stream``; returns the operations it
+    performs (time it with CUDA events on the same stream)."""
+    ops = ctypes.c_double()
+    _check(load().swept_probe_alu(int(kind), int(iters), ctypes.byref(ops), _stream(stream)),
+           "swept_probe_alu")
+    return float(ops.value)
 
 
 def swept_advance_noalloc(N: int, stencil_id: int, params, dtype: int, B: int, u, nsteps: int,

@@ -546,8 +546,9 @@ extern "C" {
 
 int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
-  if (nsteps == 0) return SWEPT_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!swept::call_on_device(p->device, s, {u})) return SWEPT_EINVAL;
+  if (nsteps == 0) return SWEPT_OK;
   if (!p->use_graph) return enqueue_advance(p, u, nsteps, s);
   // graph replay: capture the stage sequence once per (u, nsteps)
   if (!p->g_valid || p->g_u != u || p->g_nsteps != nsteps) {
@@ -636,6 +637,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
   if (!aligned16(u0) || !aligned16(lam_T) || !aligned16(grad)) return SWEPT_EINVAL;
   if (p->dtype != SWEPT_F64 || p->subs > 1 || p->nreg != p->nwin) return SWEPT_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!swept::call_on_device(p->device, s, {u0, lam_T, grad})) return SWEPT_EINVAL;
   const size_t bytes = (size_t)p->N * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(grad, lam_T, bytes, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess || nsteps == 0) return cuda_status(e);
@@ -691,6 +693,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
 int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   if (!p || !u || nsteps < 0 || !aligned16(u)) return SWEPT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!swept::call_on_device(p->device, s, {u})) return SWEPT_EINVAL;
   if (p->stencil == SWEPT_EULER && p->dtype == SWEPT_F32C) {
     // per time step: q_mid = hi + (lo - dt/(2dx) dF(hi)) into scratch, then
     // (hi', lo') = TwoSum(hi, lo - dt/dx dF(q_mid)) into scratch, swap
@@ -787,11 +790,13 @@ int swept_plan_status(swept_plan_t p, void* stream) {
 
 int swept_f32c_split(int64_t N, const double* u64, void* u32c, void* stream) {
   if (N <= 0 || !u64 || !u32c) return SWEPT_EINVAL;
+  if (!swept::call_on_device(-1, (cudaStream_t)stream, {u64, u32c})) return SWEPT_EINVAL;
   return cuda_status(swept::launch_split(N, u64, (float*)u32c, (cudaStream_t)stream));
 }
 
 int swept_f32c_merge(int64_t N, const void* u32c, double* u64, void* stream) {
   if (N <= 0 || !u64 || !u32c) return SWEPT_EINVAL;
+  if (!swept::call_on_device(-1, (cudaStream_t)stream, {u64, u32c})) return SWEPT_EINVAL;
   return cuda_status(swept::launch_merge(N, (const float*)u32c, u64, (cudaStream_t)stream));
 }
 
@@ -799,6 +804,8 @@ int swept_reduce(swept_plan_t p, const void* u, int what, const void* v, double*
   if (!p || !u || !out) return SWEPT_EINVAL;
   if (what < SWEPT_SUM || what > SWEPT_DOT) return SWEPT_EINVAL;
   if (what == SWEPT_DOT && !v) return SWEPT_EINVAL;
+  if (!swept::call_on_device(p->device, (cudaStream_t)stream, {u, what == SWEPT_DOT ? v : nullptr, out}))
+    return SWEPT_EINVAL;
   return cuda_status(swept::launch_reduce(p->dtype, u, what, (const double*)v, p->N, p->red, out,
                                           (cudaStream_t)stream));
 }

@@ -329,6 +329,7 @@ using swept::BatchProblem;
 struct swept_batch_s {
   int nprob, dtype, B_heat, B_ks, nstage_max, grid;
   int run_len;                  // windows per work item
+  int device;                   // the CUDA device the batch was planned on
   int64_t nitems, total_windows, pool_bytes;
   BatchProblem* h_probs;        // host copy, sorted by stage count (descending)
   unsigned char* edges;
@@ -548,6 +549,7 @@ int swept_batch_plan(swept_batch_t* out, int nprob, const swept_problem_t* probs
   swept_batch_s* b = (swept_batch_s*)std::calloc(1, sizeof(swept_batch_s));
   if (!b) return SWEPT_ENOMEM;
   b->nprob = nprob;
+  cudaGetDevice(&b->device);
   b->dtype = dtype;
   b->B_heat = B_heat;
   b->B_ks = B_ks;
@@ -636,6 +638,7 @@ int swept_batch_info(swept_batch_t b, int64_t* info, int ninfo) {
 int swept_advance_batch(swept_batch_t b, void* pool, void* stream) {
   if (!b || !pool || ((uintptr_t)pool & 15u)) return SWEPT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!swept::call_on_device(b->device, s, {pool})) return SWEPT_EINVAL;
   if (!b->use_graph) return cuda_status_b(enqueue(b, pool, s));
   if (!b->graph_valid || b->graph_pool != pool) {
     if (b->graph_valid) {
@@ -667,6 +670,7 @@ int swept_advance_batch(swept_batch_t b, void* pool, void* stream) {
 int swept_batch_naive_advance(swept_batch_t b, void* pool, void* stream) {
   if (!b || !pool || ((uintptr_t)pool & 15u)) return SWEPT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!swept::call_on_device(b->device, s, {pool})) return SWEPT_EINVAL;
   cudaError_t e = cudaSuccess;
   if (!b->nv_scratch) {
     e = cudaMalloc((void**)&b->nv_scratch, (size_t)b->pool_bytes);

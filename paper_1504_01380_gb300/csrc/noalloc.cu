@@ -20,7 +20,11 @@
 // Set-up: host code cannot use the array's name as a device address (it is a
 // host-side stand-in).  The first call on a device looks the address up with
 // cudaGetSymbolAddress with that device current and caches it per device;
-// make that first call before any stream capture.
+// make that first call before any stream capture.  The cache lives as long
+// as the process: after cudaDeviceReset (or anything else that destroys the
+// device's primary context) the module is loaded again and the array may
+// move, so the library must be unloaded and loaded again before the next
+// call on that device.
 #include <mutex>
 
 #include "swept.h"
@@ -71,6 +75,9 @@ extern "C" int swept_advance_noalloc(int64_t N, int stencil_id, const double* pa
   if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32) return SWEPT_ENOTSUP;
   if (K % R || N % B) return SWEPT_EINVAL;
   if (N > kMaxN) return SWEPT_ETOOBIG;
+  // u and the stream must be on the current device, whose copy of the array
+  // the kernels are given
+  if (!swept::call_on_device(-1, (cudaStream_t)stream, {u})) return SWEPT_EINVAL;
 
   // Constants, as swept_plan computes them: heat r; KS a = -(dt/(4 dx)),
   // b = -(dt/dx^2), e = -(dt/(dx^2 dx^2)), FP32 copies rounded to nearest.

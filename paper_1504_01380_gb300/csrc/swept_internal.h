@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <initializer_list>
 #include <cuda_runtime.h>
 
 #include "swept_device.cuh"
@@ -10,6 +11,41 @@ namespace swept {
 
 // Warps per thread block of the stage kernels.  One warp owns one window.
 constexpr int kWarpsPerBlock = 4;
+
+// Where a call runs.  Every device pointer an entry point takes must be
+// memory of the current CUDA device (or managed memory), the stream must
+// belong to that device, and a plan must have been made on it: a kernel
+// launched on one GPU with another GPU's pointer faults.  `plan_dev` < 0
+// means "no plan".  Checked before anything is enqueued; a failed query
+// leaves no sticky error.  (A stream whose device cannot be queried is
+// accepted: the launch itself then reports a foreign stream.)
+inline bool pointer_on_device(const void* p, int dev) {
+  if (!p) return true;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+inline bool call_on_device(int plan_dev, cudaStream_t s, std::initializer_list<const void*> ptrs) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (plan_dev >= 0 && plan_dev != dev) return false;
+  int sdev = -1;
+  if (cudaStreamGetDevice(s, &sdev) == cudaSuccess) {
+    if (sdev != dev) return false;
+  } else {
+    cudaGetLastError();
+  }
+  for (const void* p : ptrs)
+    if (!pointer_on_device(p, dev)) return false;
+  return true;
+}
 
 // Arguments of one swept stage launch (one window per warp).
 // Every field has a default, so a declared StageArgs is fully defined.

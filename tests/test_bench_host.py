@@ -53,3 +53,48 @@ def test_peak_fallback(monkeypatch, tmp_path):
     assert bench.measured_hbm_gbs() == 6800.0
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6793.2}')
     assert bench.measured_hbm_gbs() == 6793.2
+
+
+def test_traffic_only_from_a_capture_of_the_current_sources(monkeypatch, tmp_path):
+    """The roofline's DRAM traffic comes from a committed ncu summary only while the kernel
+    sources it was captured from are unchanged (their digest is written in the summary)."""
+    csrc = tmp_path / "paper_1504_01380_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "a.cuh").write_text("kernel v1")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    prof = tmp_path / "p.md"
+    assert bench.profile_traffic(str(prof), ("a.cuh",))[0] is None            # no file
+    digest = bench.source_digest(("a.cuh",))
+    body = ("- dram__bytes_read.sum = 10.5 Gbyte\n- dram__bytes_write.sum = 2.25 Gbyte\n")
+    prof.write_text(body)
+    assert bench.profile_traffic(str(prof), ("a.cuh",))[0] is None            # no digest recorded
+    prof.write_text(f"source digest: `{digest}`\n" + body)
+    t, note = bench.profile_traffic(str(prof), ("a.cuh",))
+    assert t == 12.75e9 and "current" in note
+    (csrc / "a.cuh").write_text("kernel v2")                                  # the kernel changed
+    t, note = bench.profile_traffic(str(prof), ("a.cuh",))
+    assert t is None and "changed" in note
+
+
+def test_alu_peak_fallback_is_the_nominal_rate(monkeypatch, tmp_path):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peak, unit, source, nominal = bench.peak_block(None, "fp32")
+    assert peak == nominal == 152 * 128 * 2070e6 and source.startswith("nominal")
+    measured = {"fp32_ops_per_s": 38e12, "f32_fma": {"sm_mhz": 2070},
+                "fp64_flop_per_s": 1.2e12, "f64_fma": {"sm_mhz": 2070}}
+    assert bench.peak_block(measured, "fp32")[0] == 38e12
+    assert bench.peak_block(measured, "fp64")[0] == 1.2e12
+    assert bench.peak_block(None, "fp64")[0] is None
+    r = bench.roofline(19e12, 38e12, "FP32 ops/s", "measured")
+    assert r["frac"] == 0.5 and r["achieved"] == 19.0 and r["peak"] == 38.0
+
+
+def test_exact_heat_closed_form():
+    """The bench's error reference: a single Fourier mode is scaled by g_k^n, and the mean is kept."""
+    import numpy as np
+    n, k, r, steps = 64, 3, 0.25, 37
+    x = np.arange(n)
+    u0 = 2.0 + np.sin(2 * np.pi * k * x / n)
+    g = 1 - 4 * r * np.sin(np.pi * k / n) ** 2
+    want = 2.0 + g ** steps * np.sin(2 * np.pi * k * x / n)
+    assert np.max(np.abs(bench.exact_heat(u0, r, steps) - want)) < 1e-13

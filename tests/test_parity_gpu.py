@@ -218,12 +218,14 @@ def test_full_size_heat_2p24(cuda_lib, dtype):
     assert np.max(np.abs(vals - spec)) <= tol * np.max(np.abs(u0))
 
 
-@pytest.mark.parametrize("dtype", [F64, F32C])
-def test_full_size_ks_2p22(cuda_lib, dtype):
-    """KS N = 2^22, B = 256: 2000 steps against oracle samples; FP32C error vs FP64 oracle."""
+@pytest.mark.parametrize("dtype,B", [(F64, 256), (F32C, 256), (F32C, 512)])
+def test_full_size_ks_2p22(cuda_lib, dtype, B):
+    """KS N = 2^22: 2000 steps against oracle samples; FP32C error vs FP64 oracle.  B = 512 in
+    compensated FP32 is the launch configuration the benchmark's KS report times (the streamed
+    ring over runs of 3-4 windows per warp); B = 256 is the FP64 report's."""
     sw = cuda_lib
     N, nsteps = 1 << 22, 2000
-    plan = sw.swept_plan(N, 2, KS, list(KS_PRM), dtype, 256)
+    plan = sw.swept_plan(N, 2, KS, list(KS_PRM), dtype, B)
     u0 = workloads.ks_smoothed(N)
     got = run_gpu(sw, plan, u0, nsteps)
     naive = run_gpu(sw, plan, u0, nsteps, naive=True)

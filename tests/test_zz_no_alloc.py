@@ -51,6 +51,51 @@ def test_noalloc_matches_swept_advance_twice(cuda_lib, stencil, dtype, B, N):
     plan.destroy()
 
 
+@pytest.mark.parametrize("stencil,dtype,B", [(0, 0, 64), (0, 1, 128), (1, 0, 128), (1, 1, 64)])
+def test_noalloc_schedule_edges(cuda_lib, stencil, dtype, B):
+    """Step counts at the ends of the schedule, two calls in a row each: fewer than h (no full
+    triangle: a trapezoid and its fill), exactly h and h + 1 (one triangle, then the last fill
+    with and without a remainder stage), and 0 (a no-op that leaves u untouched)."""
+    import torch
+    sw = cuda_lib
+    prm = [0.25] if stencil == 0 else KS_PRM
+    radius = 1 if stencil == 0 else 2
+    N = 5 * B
+    plan = sw.swept_plan(N, radius, stencil, prm, dtype, B)
+    h = plan.h
+    for i, nsteps in enumerate((h // 2, 1, h, h + 1, 0)):
+        u0 = workloads.uniform(N, 40 + i) if stencil == 0 else 10 * workloads.ks_smoothed(N, 40 + i)
+        ref = _state(sw, dtype, u0)
+        sw.swept_advance(plan, ref, nsteps)
+        for _ in range(2):
+            got = _state(sw, dtype, u0)
+            sw.swept_advance_noalloc(N, stencil, prm, dtype, B, got, nsteps)
+            torch.cuda.synchronize()
+            assert torch.equal(got, ref), f"nsteps={nsteps}: no-allocation result differs"
+        if nsteps == 0:
+            assert torch.equal(got, _state(sw, dtype, u0))
+    plan.destroy()
+
+
+def test_noalloc_rejects_what_it_does_not_take(cuda_lib):
+    """Uneven tiles (N not a multiple of B), the plain binary32 state and the other stencils
+    are the plan's, not this entry point's: each is refused before anything runs."""
+    import torch
+    sw = cuda_lib
+    u = torch.zeros(2 * 1056, dtype=torch.float64, device="cuda")
+    before = u.clone()
+    cases = [(1056, sw.SWEPT_HEAT, [0.25], sw.SWEPT_F64, 64),        # 1056 = 16.5 tiles of 64
+             (1024, sw.SWEPT_HEAT, [0.25], sw.SWEPT_F32, 64),        # plain binary32
+             (1024, sw.SWEPT_HEAT_RK2, [0.25], sw.SWEPT_F64, 64),    # Runge-Kutta
+             (1024, sw.SWEPT_KS, KS_PRM, sw.SWEPT_F64, 32)]          # K = 1 < radius 2
+    for N, stencil, prm, dtype, B in cases:
+        with pytest.raises(sw.SweptError) as ei:
+            sw.swept_advance_noalloc(N, stencil, prm, dtype, B, u, 10)
+        assert ei.value.code == sw.SWEPT_EINVAL, (N, stencil, dtype, B)
+    torch.cuda.synchronize()
+    assert torch.equal(u, before)
+
+
 def test_noalloc_rejects_oversize(cuda_lib):
     import torch
     sw = cuda_lib
