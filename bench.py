@@ -889,7 +889,7 @@ def report_adjoint_c4(peaks, flush):
     sw.swept_adjoint(plan, u0, uT, nsteps, K, out=g)                       # warm-up (allocates)
     torch.cuda.synchronize()
     t_grad = cuda_time(lambda: sw.swept_adjoint(plan, u0, uT, nsteps, K, out=g))
-    scratch = sw.swept_adjoint_scratch(plan, nsteps, K) if "swept_adjoint_scratch" in dir(sw) else None
+    scratch = sw.swept_adjoint_scratch(plan, nsteps, K)
     w = torch.empty_like(u0)
     jbuf = torch.empty(1, dtype=torch.float64, device="cuda")
 

@@ -16,7 +16,9 @@
  *     them.  A plan or batch is used on the device it was made on, with a
  *     stream of that device.  Each entry point checks this before it
  *     enqueues anything and returns SWEPT_EINVAL otherwise (a kernel given
- *     another GPU's pointer would fault).
+ *     another GPU's pointer would fault).  While the stream is being captured
+ *     into a CUDA graph only the plan's device is checked (the pointer
+ *     queries would end the capture): the caller vouches for the pointers.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls enqueue work on it and return without synchronising
  *     unless stated otherwise.
@@ -265,19 +267,33 @@ int swept_plan_last_advance(swept_plan_t plan, int64_t *launches, int64_t *ring_
  *   KS:   lambda'_j = lambda_j + 2a u_j (lambda_{j-1} - lambda_{j+1})
  *                     + b (L2 lambda)_j + e (L2 L2 lambda)_j,
  * u_j the forward state at that level.  The cotangent is advanced backwards
- * in time by the swept rule (same stages, transposed stencil).  KS needs the
- * forward state at every level: the forward pass keeps a checkpoint of u
- * every 2*K_cycles*h levels (K_cycles swept cycles of two stages; <= 0 means
- * 64), and each segment is recomputed from its checkpoint into a tape that
- * the reverse sweep reads.  FP64 plans only.
+ * in time by the swept rule (same stages, transposed stencil), one stage per
+ * launch.  KS needs the forward state at every level (checkpoints plus
+ * recomputation): the forward pass is one swept advance whose kernels also
+ * store the flat level that ends every m-th stage (a checkpoint every m*h
+ * levels, nothing extra to compute); the reverse pass recomputes the forward
+ * levels from those checkpoints, m*h at a time and each once, by per-step
+ * stepping into a ring of m + 1 chunks of h levels, from which each
+ * transposed stage reads its 2h levels.  m is at most 2*K_cycles stages
+ * (K_cycles swept cycles of two stages; <= 0 means 64) and is the value that
+ * minimises the scratch.  FP64 plans on even tiles only.
  *   u0, lambda_T, grad_u0  device double[N]; grad_u0 may not alias u0.
- * Scratch (plan-owned, grown on demand): (1 + segments + 2*K_cycles*h) * 8N
- * bytes for KS; none for heat.
- * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP (F32C, Runge-Kutta or Euler plan),
- * SWEPT_ENOMEM, SWEPT_ECUDA.
+ * Scratch (plan-owned, grown on demand, kept until swept_destroy), for KS
+ * with nsteps = q*h + rem:
+ *   8N * ([rem > 0] + ceil(q/m) + (m + 1)*h) bytes
+ * (swept_adjoint_scratch returns it; N = 2^20, 20000 steps, h = 64: m = 2,
+ * 349 states, 2.9 GB); none for heat.
+ * Errors: SWEPT_EINVAL (null or misaligned pointers, grad_u0 == u0, memory of
+ * another device), SWEPT_ENOTSUP (F32C, F32, Runge-Kutta, Euler or uneven
+ * plan), SWEPT_ENOMEM (the scratch does not fit), SWEPT_ECUDA.
  */
 int swept_adjoint(swept_plan_t plan, const void *u0, const void *lambda_T, void *grad_u0,
                   int64_t nsteps, int K_cycles, void *stream);
+
+/* Device scratch, in bytes, that swept_adjoint(plan, ..., nsteps, K_cycles)
+ * allocates (the bound above); *bytes = 0 for heat.  Errors: SWEPT_EINVAL,
+ * SWEPT_ENOTSUP (a plan swept_adjoint does not take). */
+int swept_adjoint_scratch(swept_plan_t plan, int64_t nsteps, int K_cycles, int64_t *bytes);
 
 /* ---- FP32-compensated state conversion -------------------------------- */
 

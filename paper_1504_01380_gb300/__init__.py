@@ -35,7 +35,7 @@ EXPORTS = (
     "swept_advance_noalloc", "swept_plan_set",
     "swept_batch_plan", "swept_batch_set", "swept_batch_info", "swept_advance_batch",
     "swept_batch_status", "swept_batch_destroy", "swept_adjoint", "swept_batch_naive_advance",
-    "swept_plan_status", "swept_plan_last_advance", "swept_probe_alu",
+    "swept_plan_status", "swept_plan_last_advance", "swept_probe_alu", "swept_adjoint_scratch",
 )
 
 SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH, SWEPT_BOPT_RUN_LEN = 0, 1, 2, 3, 4
@@ -110,6 +110,8 @@ def load(path: str | None = None):
         L.swept_batch_destroy.restype = None
         L.swept_adjoint.argtypes = [vp, vp, vp, vp, i64, i32, vp]
         L.swept_adjoint.restype = i32
+        L.swept_adjoint_scratch.argtypes = [vp, i64, i32, ctypes.POINTER(i64)]
+        L.swept_adjoint_scratch.restype = i32
         L.swept_probe_alu.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), vp]
         L.swept_probe_alu.restype = i32
         L.swept_strerror.argtypes = [i32]
@@ -388,6 +390,14 @@ def swept_adjoint(plan: Plan, u0, lam_T, nsteps: int, K_cycles: int = 64, out=No
                                 _dev_ptr(out, plan.state_bytes, "grad"), int(nsteps), int(K_cycles),
                                 _stream(stream)), "swept_adjoint")
     return out
+
+
+def swept_adjoint_scratch(plan: Plan, nsteps: int, K_cycles: int = 64) -> int:
+    """Device bytes swept_adjoint allocates for this plan, step count and checkpoint bound."""
+    b = ctypes.c_int64()
+    _check(load().swept_adjoint_scratch(plan.handle, int(nsteps), int(K_cycles), ctypes.byref(b)),
+           "swept_adjoint_scratch")
+    return int(b.value)
 
 
 def _make_autograd():

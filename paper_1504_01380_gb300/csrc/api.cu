@@ -421,13 +421,22 @@ bool stream_ok(const swept_plan_s* p, int64_t q) {
   return true;
 }
 
+// Flat checkpoints an advance stores on the way (the adjoint's forward pass):
+// the level that ends stage k's V-fill goes to ckpt + (k / every) * N for
+// 0 < k < kmax, k % every == 0 (StageArgs::ckpt).
+struct Dumps {
+  double* ckpt;
+  int every;
+  int64_t kmax;
+};
+
 // Enqueue the stage sequence of one advance (Section 3's stages, A5's schedule).
-int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
+int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s, const Dumps* dumps = nullptr) {
   const int64_t levels = p->subs * nsteps;                // sub-timesteps
   const int64_t H = p->H;
   const int64_t q = levels / H;
   const int rem = (int)(levels % H);
-  if (persistent_ok(p, levels)) {
+  if (!dumps && persistent_ok(p, levels)) {
     swept::PersistArgs pa{};
     pa.a.u = u;
     pa.a.N = p->N;
@@ -463,6 +472,11 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s) {
   a.nwin = p->nwin;
   a.c = p->c;
   a.pdl = p->pdl;
+  if (dumps) {
+    a.ckpt = dumps->ckpt;
+    a.ckpt_every = dumps->every;
+    a.ckpt_kmax = dumps->kmax;
+  }
   // stage k: windows shifted by B/2 when k is odd (the alternating point
   // sets of Section 3); reads the edges of stage k-1, writes its own.
   const bool uneven = p->nreg != p->nwin;
@@ -584,23 +598,127 @@ int swept_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
 
 namespace {
 
-// Swept sweep of the adjoint variable lam over `len` levels of the transposed
-// KS step; level tau of the sweep uses the forward state tape[len - tau].
-// Same stage schedule as swept_advance.
-cudaError_t adjoint_sweep(swept_plan_s* p, double* lam, int64_t len, const double* tape, cudaStream_t s) {
+// Scratch of the KS adjoint.  The forward pass is one swept advance that
+// also stores the flat level ending every m-th stage (a flat checkpoint every
+// m*h levels, m = `every`); the reverse pass recomputes the forward levels
+// from those checkpoints, m*h at a time, with the naive stepper (every level
+// is computed once more, as in any checkpointed adjoint) into a ring of m + 1
+// chunks of h levels, and sweeps the cotangent back one stage at a time,
+// each stage reading at most two chunks.  nsteps = q*h + rem is advanced as
+// rem levels first, so that the long advance's stage boundaries are the
+// sweep's (forward level rem + k*h = sweep level (q - k)*h).  Scratch, in
+// states of 8N bytes: the level-0 state (when rem > 0) + ceil(q/m)
+// checkpoints + (m + 1)*h tape levels; m (at most 2*K_cycles stages, K_cycles
+// swept cycles of two stages) is the one that minimises it.
+struct AdjLayout {
+  int64_t q = 0, rem = 0, every = 1, nckpt = 0, ring = 0, states = 0;
+};
+
+AdjLayout adjoint_layout(const swept_plan_s* p, int64_t nsteps, int K_cycles) {
+  AdjLayout L;
   const int64_t H = p->H;
-  const int64_t q = len / H;
-  const int rem = (int)(len % H);
+  L.q = nsteps / H;
+  L.rem = nsteps % H;
+  if (K_cycles <= 0) K_cycles = 64;
+  const int64_t mmax = 2 * (int64_t)K_cycles;
+  int64_t best = -1;
+  for (int64_t m = 1; m <= mmax && m <= (L.q > 1 ? L.q : 1); ++m) {
+    const int64_t states = (L.q + m - 1) / m + (m + 1) * H;
+    if (best < 0 || states < best) {
+      best = states;
+      L.every = m;
+    }
+  }
+  L.nckpt = L.q > 0 ? (L.q + L.every - 1) / L.every : 0;
+  L.ring = L.every + 1;
+  L.states = (L.rem > 0 ? 1 : 0) + L.nckpt + L.ring * H;
+  return L;
+}
+
+// Host mirror of tape_level(): the ring slot of forward level l.
+double* tape_at(double* ring, const AdjLayout& L, int64_t H, int64_t N, int64_t l) {
+  int64_t slot, off;
+  if (l < L.rem) {
+    slot = L.ring - 1;
+    off = l;
+  } else {
+    const int64_t c = (l - L.rem) / H;
+    off = l - L.rem - c * H;
+    slot = c % L.ring;
+  }
+  return ring + (slot * H + off) * N;
+}
+
+int adjoint_ks(swept_plan_s* p, const double* u0, double* lam, int64_t F, const AdjLayout& L, double* scratch,
+               cudaStream_t s) {
+  const int64_t N = p->N, H = p->H;
+  const size_t bytes = (size_t)N * sizeof(double);
+  double* pre = scratch;                                   // level 0 (rem > 0)
+  double* ckpt = pre + (L.rem > 0 ? N : 0);                // level rem + g*every*H, g < nckpt
+  double* ring = ckpt + L.nckpt * N;                       // the tape ring
+  cudaError_t e = cudaSuccess;
+  // ---- forward pass: checkpoints
+  if (L.rem > 0) e = cudaMemcpyAsync(pre, u0, bytes, cudaMemcpyDeviceToDevice, s);
+  if (L.q > 0) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ckpt, u0, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && L.rem > 0) {
+      const int rc = enqueue_advance(p, ckpt, L.rem, s);     // level rem
+      if (rc != SWEPT_OK) return rc;
+    }
+    // the long advance runs in the ring's memory (free until the reverse pass)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ring, ckpt, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && L.nckpt > 1) {
+      const Dumps d{ckpt, (int)L.every, L.q};
+      const int rc = enqueue_advance(p, ring, L.q * H, s, &d);
+      if (rc != SWEPT_OK) return rc;
+    }
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  // ---- reverse pass.  Chunk c >= 0 holds forward levels rem + c*H .. + H - 1,
+  // chunk -1 levels 0 .. rem - 1; chunks >= `lowest` are in the ring.
+  int64_t lowest = L.q;
+  auto recompute_down_to = [&](int64_t need) -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    while (lowest > need && r == cudaSuccess) {
+      const int64_t top = lowest - 1;
+      int64_t l0, count;
+      const double* from;
+      if (top >= 0) {                                     // the checkpoint group holding chunk top
+        const int64_t g = top / L.every;
+        l0 = L.rem + g * L.every * H;
+        count = (lowest - g * L.every) * H;
+        from = ckpt + g * N;
+        lowest = g * L.every;
+      } else {
+        l0 = 0;
+        count = L.rem;
+        from = pre;
+        lowest = -1;
+      }
+      r = cudaMemcpyAsync(tape_at(ring, L, H, N, l0), from, bytes, cudaMemcpyDeviceToDevice, s);
+      for (int64_t l = l0 + 1; l < l0 + count && r == cudaSuccess; ++l)
+        r = swept::launch_naive_step(p->stencil, p->dtype, tape_at(ring, L, H, N, l - 1),
+                                     tape_at(ring, L, H, N, l), N, p->c, s, p->pdl != 0);
+    }
+    return r;
+  };
+  // the sweep: swept_advance's stage schedule on lam, transposed stencil;
+  // sweep level tau reads forward level F - tau
   unsigned char* buf[2] = {p->edges, p->edges + p->edge_half};
   StageArgs a{};
   a.u = lam;
-  a.N = p->N;
+  a.N = N;
   a.nwin = p->nwin;
   a.c = p->c;
-  a.tape = tape;
-  a.tape_len = len;
+  a.tape = ring;
+  a.tape_len = F;
+  a.tape_ring = (int)L.ring;
+  a.tape_h = (int)H;
+  a.tape_rem = (int)L.rem;
   a.pdl = p->pdl;
-  auto stage = [&](int64_t k, int hv, int ht) -> cudaError_t {
+  auto stage = [&](int64_t k, int hv, int ht, int64_t need) -> cudaError_t {
+    cudaError_t r = recompute_down_to(need);
+    if (r != cudaSuccess) return r;
     a.offset = (k & 1) ? p->B / 2 : 0;
     a.hv = hv;
     a.ht = ht;
@@ -614,22 +732,32 @@ cudaError_t adjoint_sweep(swept_plan_s* p, double* lam, int64_t len, const doubl
     }
     return swept::launch_stage_ksadj_f64(p->K, a, s);
   };
-  cudaError_t e = cudaSuccess;
+  const int64_t q = L.q;
+  const int rem = (int)L.rem;
   if (q == 0) {
-    e = stage(0, 0, rem);
-    if (e == cudaSuccess) e = stage(1, rem, 0);
+    e = stage(0, 0, rem, -1);
+    if (e == cudaSuccess) e = stage(1, rem, 0, -1);
   } else {
-    e = stage(0, 0, (int)H);
-    for (int64_t k = 1; k < q && e == cudaSuccess; ++k) e = stage(k, (int)H, (int)H);
-    if (e == cudaSuccess) e = stage(q, (int)H, rem);
-    if (e == cudaSuccess && rem > 0) e = stage(q + 1, rem, 0);
+    e = stage(0, 0, (int)H, q - 1);
+    for (int64_t k = 1; k < q && e == cudaSuccess; ++k) e = stage(k, (int)H, (int)H, q - k - 1);
+    if (e == cudaSuccess) e = stage(q, (int)H, rem, rem > 0 ? -1 : 0);
+    if (e == cudaSuccess && rem > 0) e = stage(q + 1, rem, 0, -1);
   }
-  return e;
+  return cuda_status(e);
 }
 
 }  // namespace
 
 extern "C" {
+
+int swept_adjoint_scratch(swept_plan_t p, int64_t nsteps, int K_cycles, int64_t* bytes) {
+  if (!p || !bytes || nsteps < 0) return SWEPT_EINVAL;
+  if (p->dtype != SWEPT_F64 || p->subs > 1 || p->nreg != p->nwin) return SWEPT_ENOTSUP;
+  *bytes = 0;
+  if (p->stencil == SWEPT_KS && nsteps > 0)
+    *bytes = adjoint_layout(p, nsteps, K_cycles).states * p->N * (int64_t)sizeof(double);
+  return SWEPT_OK;
+}
 
 int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad, int64_t nsteps,
                   int K_cycles, void* stream) {
@@ -638,6 +766,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
   if (p->dtype != SWEPT_F64 || p->subs > 1 || p->nreg != p->nwin) return SWEPT_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   if (!swept::call_on_device(p->device, s, {u0, lam_T, grad})) return SWEPT_EINVAL;
+  if (u0 == grad) return SWEPT_EINVAL;
   const size_t bytes = (size_t)p->N * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(grad, lam_T, bytes, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess || nsteps == 0) return cuda_status(e);
@@ -646,12 +775,8 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
     // same update with the same rounding: the adjoint is the forward sweep.
     return swept_advance(p, grad, nsteps, stream);
   }
-  if (K_cycles <= 0) K_cycles = 64;
-  int64_t C = 2 * (int64_t)K_cycles * p->H;      // levels per checkpoint segment
-  if (C > nsteps) C = nsteps;
-  const int64_t nseg = (nsteps + C - 1) / C;
-  // scratch: work state (1) + checkpoints (nseg) + tape (C levels)
-  const size_t need = (size_t)(1 + nseg + C) * bytes;
+  const AdjLayout L = adjoint_layout(p, nsteps, K_cycles);
+  const size_t need = (size_t)L.states * bytes;
   if (p->adj_bytes < need) {
     cudaStreamSynchronize(s);
     if (p->adj) cudaFree(p->adj);
@@ -664,30 +789,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
     }
     p->adj_bytes = need;
   }
-  double* work = p->adj;
-  double* ckpt = work + p->N;
-  double* tape = ckpt + nseg * p->N;
-  // forward pass with a checkpoint at the start of every segment
-  e = cudaMemcpyAsync(work, u0, bytes, cudaMemcpyDeviceToDevice, s);
-  for (int64_t g = 0; g < nseg && e == cudaSuccess; ++g) {
-    e = cudaMemcpyAsync(ckpt + g * p->N, work, bytes, cudaMemcpyDeviceToDevice, s);
-    const int64_t len = (g + 1 < nseg) ? C : nsteps - g * C;
-    if (e == cudaSuccess && g + 1 < nseg) {
-      const int rc = swept_advance(p, work, len, stream);
-      if (rc != SWEPT_OK) return rc;
-    }
-  }
-  // reverse: recompute each segment's trajectory into the tape, then sweep
-  double* lam = static_cast<double*>(grad);
-  for (int64_t g = nseg - 1; g >= 0 && e == cudaSuccess; --g) {
-    const int64_t len = (g + 1 < nseg) ? C : nsteps - g * C;
-    e = cudaMemcpyAsync(tape, ckpt + g * p->N, bytes, cudaMemcpyDeviceToDevice, s);
-    for (int64_t n = 1; n < len && e == cudaSuccess; ++n)
-      e = swept::launch_naive_step(p->stencil, p->dtype, tape + (n - 1) * p->N, tape + n * p->N, p->N,
-                                   p->c, s, p->pdl != 0);
-    if (e == cudaSuccess) e = adjoint_sweep(p, lam, len, tape, s);
-  }
-  return cuda_status(e);
+  return adjoint_ks(p, static_cast<const double*>(u0), static_cast<double*>(grad), nsteps, L, p->adj, s);
 }
 
 int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {

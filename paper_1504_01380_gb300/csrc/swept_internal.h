@@ -18,7 +18,11 @@ constexpr int kWarpsPerBlock = 4;
 // launched on one GPU with another GPU's pointer faults.  `plan_dev` < 0
 // means "no plan".  Checked before anything is enqueued; a failed query
 // leaves no sticky error.  (A stream whose device cannot be queried is
-// accepted: the launch itself then reports a foreign stream.)
+// accepted: the launch itself then reports a foreign stream.)  While `s` is
+// being captured into a CUDA graph the pointer and stream queries would end
+// the capture, so only the plan's device is checked then; otherwise the
+// queries run in relaxed capture mode, so that they cannot disturb a
+// capture another thread has open.
 inline bool pointer_on_device(const void* p, int dev) {
   if (!p) return true;
   cudaPointerAttributes at{};
@@ -36,15 +40,25 @@ inline bool call_on_device(int plan_dev, cudaStream_t s, std::initializer_list<c
     return false;
   }
   if (plan_dev >= 0 && plan_dev != dev) return false;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return true;
+  cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+  cudaThreadExchangeStreamCaptureMode(&mode);
+  bool ok = true;
   int sdev = -1;
   if (cudaStreamGetDevice(s, &sdev) == cudaSuccess) {
-    if (sdev != dev) return false;
+    ok = sdev == dev;
   } else {
     cudaGetLastError();
   }
   for (const void* p : ptrs)
-    if (!pointer_on_device(p, dev)) return false;
-  return true;
+    if (ok && !pointer_on_device(p, dev)) ok = false;
+  cudaThreadExchangeStreamCaptureMode(&mode);
+  return ok;
 }
 
 // Arguments of one swept stage launch (one window per warp).
@@ -59,13 +73,25 @@ struct StageArgs {
   int hv = 0;                  // V-fill height (0 = load the flat state instead)
   int ht = 0;                  // trapezoid height (0 = none; h = full triangle)
   Consts c{};
-  // Adjoint sweeps only: the forward trajectory of the segment, level n at
-  // tape + n*N (FP64), tape_len levels; the sweep's level tau uses the
-  // forward level tape_len - tau.  lev_fill / lev_trap: sweep level of the
-  // V-fill's base and of the trapezoid's flat base.
+  // Adjoint sweeps only: the forward trajectory, tape_len levels; the
+  // sweep's level tau uses the forward level tape_len - tau, found by
+  // tape_level() below: level n at tape + n*N when tape_ring is
+  // 0, else in a ring of tape_ring chunks of tape_h levels (chunk c holds
+  // levels tape_rem + c*tape_h ... at slot c mod tape_ring; levels below
+  // tape_rem in the last slot).  lev_fill / lev_trap: sweep level of the
+  // V-fill's base and of the trapezoid's flat base (also the stage index
+  // times h: lev_trap = k*h for stage k).
   const double* tape = nullptr;
   int64_t tape_len = 0;
+  int tape_ring = 0, tape_h = 0, tape_rem = 0;
   int64_t lev_fill = 0, lev_trap = 0;
+  // Flat checkpoints of a forward FP64 KS advance (the adjoint's forward
+  // pass): the V-fill of stage k ends with the window flat at level k*h of
+  // the advance; when ckpt is set, 0 < k < ckpt_kmax and k % ckpt_every == 0
+  // the kernels also store it to ckpt + (k / ckpt_every) * N.
+  double* ckpt = nullptr;
+  int ckpt_every = 0;
+  int64_t ckpt_kmax = 0;
   int pdl = 0;                 // launch with programmatic dependent launch (host side only)
   int nlaunch = 0;             // windows launched (0: nwin); uneven tiles launch the regular ones only
   // Streamed ring launches: full-diamond stages run by one launch (0 or 1:
@@ -78,6 +104,28 @@ struct StageArgs {
   long long budget = 0;
   int drop = -1;               // failure injection: this warp never publishes its slot counter
 };
+
+// Forward level l of an adjoint sweep's tape (see StageArgs::tape).
+__device__ __forceinline__ const double* tape_level(const StageArgs& a, int64_t l) {
+  if (a.tape_ring == 0) return a.tape + l * a.N;
+  const int li = (int)l;
+  int slot, off;
+  if (li < a.tape_rem) {
+    slot = a.tape_ring - 1;
+    off = li;
+  } else {
+    const int c = (li - a.tape_rem) / a.tape_h;
+    off = li - a.tape_rem - c * a.tape_h;
+    slot = c % a.tape_ring;
+  }
+  return a.tape + ((int64_t)slot * a.tape_h + off) * a.N;
+}
+
+// Where the flat level that ends stage k's V-fill is checkpointed, or nullptr.
+__device__ __forceinline__ double* ckpt_of(const StageArgs& a, int64_t k) {
+  if (!a.ckpt || k <= 0 || k >= a.ckpt_kmax || k % a.ckpt_every) return nullptr;
+  return a.ckpt + (k / a.ckpt_every) * a.N;
+}
 
 // Launch `kern` on `s`; with pdl, as a programmatic dependent launch (the
 // kernel may be scheduled while the previous kernel on the stream runs, and

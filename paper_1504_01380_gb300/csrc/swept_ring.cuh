@@ -174,8 +174,8 @@ struct RingImpl {
     constexpr int M = 32 * S;
     const int lo_f = B / 2 - R * (mp + 1), hi_f = B / 2 + R * (mp + 1);
     const int lo_t = R * (mp + 1), hi_t = B - R * (mp + 1);
-    const double* rf = a.tape + (a.tape_len - (a.lev_fill + mp + 1)) * a.N;
-    const double* rt = a.tape + (a.tape_len - (a.lev_trap + mp + 1)) * a.N;
+    const double* rf = tape_level(a, a.tape_len - (a.lev_fill + mp + 1));
+    const double* rt = tape_level(a, a.tape_len - (a.lev_trap + mp + 1));
     const int64_t wsf = (int64_t)wfill * B + a.offset;
     const int64_t wst = wsf - B;                       // the emptied window is wfill - 1
 #pragma unroll
@@ -194,6 +194,30 @@ struct RingImpl {
         v = rt[g];
       }
       cf[k] = v;
+    }
+  }
+
+  // After a slot, the filled window sits flat at ring positions [0, B) from
+  // the fill offset: ring position p = ((lane - cl) mod 32) * S + k is window
+  // point p.  Store it as the forward pass's checkpoint when its stage k is
+  // one (StageArgs::ckpt); ws is the window's first global point.
+  static __device__ __forceinline__ void dump_fill(const Tile<DT, S>& t, const StageArgs& a, int lane, int cl,
+                                                   int64_t k, int64_t ws) {
+    if constexpr (DumpsCkpt<ST, DT>::value) {
+      double* ck = ckpt_of(a, k);
+      if (!ck) return;
+      const int rel = (lane - cl) & 31;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const int p = rel * S + j;
+        if (p < B) {
+          int64_t g = ws + p;
+          if (g >= a.N) g -= a.N;
+          ck[g] = t.get(j);
+        }
+      }
+    } else {
+      (void)t; (void)a; (void)lane; (void)cl; (void)k; (void)ws;
     }
   }
 
@@ -285,6 +309,7 @@ struct RingImpl {
       __syncwarp();
       slot_levels(t, a, s0, s1, lane, cl, fill, empty, a.lev_fill, w0 + slot);
       __syncwarp();
+      if (fill) dump_fill(t, a, lane, cl, a.lev_trap / H, (int64_t)(w0 + slot) * B + a.offset);
       if (empty) {
         const int ws = w0 + slot - 1;
         warp_copy(eout + (int64_t)ws * (2 * B), s0, B, lane);
@@ -376,6 +401,11 @@ struct RingImpl {
       __syncwarp();
       slot_levels(t, a, s0, s1, lane, cl, fill, empty, a.lev_fill + (int64_t)jf * H, 0);
       __syncwarp();
+      if (fill) {
+        const bool offs = ((jf + odd0) & 1) != 0;
+        const int w = (w0 + ((jf + odd0) >> 1) + i_f) % a.nwin;
+        dump_fill(t, a, lane, cl, a.lev_trap / H + jf, (int64_t)w * B + (offs ? B / 2 : 0));
+      }
       if (empty) {
         const int w = (w0 + ((je + odd0) >> 1) + ie) % a.nwin;
         E* eout = static_cast<E*>((je & 1) ? const_cast<void*>(a.ein) : a.eout);

@@ -41,6 +41,11 @@
 
 namespace swept {
 
+// Kernels that store flat checkpoints when asked (StageArgs::ckpt): the FP64
+// KS forward advance, whose states the adjoint's transposed step needs.
+template <int ST, class DT> struct DumpsCkpt { static constexpr bool value = false; };
+template <> struct DumpsCkpt<kKS, F64> { static constexpr bool value = true; };
+
 template <int ST, class DT, int K>
 struct StageImpl {
   using E = typename DT::E;
@@ -64,7 +69,7 @@ struct StageImpl {
     if constexpr (ST == kKSAdj) {
       int64_t g = ws + (int64_t)lane * K;
       if (g >= a.N) g -= a.N;
-      ld_chunk<K>(a.tape + (a.tape_len - tau) * a.N + g, cf.u);
+      ld_chunk<K>(tape_level(a, a.tape_len - tau) + g, cf.u);
     } else if constexpr (Subs<ST>::value > 1) {
       cf.sub = (int)((tau - 1) & (Subs<ST>::value - 1));
       (void)a; (void)ws; (void)lane;
@@ -274,6 +279,16 @@ struct StageImpl {
       __syncwarp();
       vfill(t, sL, sR, a.hv, lane, a, ws);
       __syncwarp();
+      if constexpr (DumpsCkpt<ST, DT>::value) {
+        // a full fill leaves the window flat: the forward pass's checkpoint
+        if (a.hv == H) {
+          if (double* ck = ckpt_of(a, a.lev_trap / H)) {
+            int64_t g = ws + (int64_t)lane * K;
+            if (g >= N) g -= N;
+            store_points<K>(t, ck, N, g);
+          }
+        }
+      }
     }
     if (a.ht > 0) {
       trapezoid(t, sL, sR, a.ht, lane, a, ws);

@@ -61,6 +61,70 @@ def test_ks_adjoint_ring_sweep_matches_oracle(cuda_lib, B, warps):
         assert np.array_equal(got, oracle.adjoint_f64(1, KS_PRM, u0, lam, nsteps)), (nsteps, K)
 
 
+@pytest.mark.parametrize("stream", [1, 0])
+def test_ks_adjoint_checkpoint_dumps_every_kernel(cuda_lib, stream):
+    """The forward pass's flat checkpoints are stored by whichever kernel runs the stage: the
+    streamed ring (stream = 1), one ring launch per stage (stream = 0), and the per-window
+    kernel (few windows).  Checkpoint intervals of 1 to 4 stages and step counts around the
+    stage boundaries, bit-exact against the oracle's discrete adjoint."""
+    sw = cuda_lib
+    B = 128
+    for nwin, ring in ((24, True), (4, False)):
+        n = nwin * B
+        u0 = workloads.ks_smoothed(n, 21) * 10
+        lam = workloads.uniform(n, 22)
+        plan = sw.swept_plan(n, 2, sw.SWEPT_KS, KS_PRM, sw.SWEPT_F64, B)
+        if ring:
+            sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+            sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, 4)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_STREAM, stream)
+        h = plan.h
+        for nsteps, K in ((9 * h, 1), (9 * h + 5, 2), (13 * h + h - 1, 1), (2 * h + 1, 64), (h - 3, 1)):
+            got = sw.swept_adjoint(plan, dev(u0), dev(lam), nsteps, K).cpu().numpy()
+            assert np.array_equal(got, oracle.adjoint_f64(1, KS_PRM, u0, lam, nsteps)), (nwin, nsteps, K)
+        plan.destroy()
+
+
+def test_adjoint_scratch_is_bounded(cuda_lib):
+    """The scratch is 8N * ([rem > 0] + ceil(q/m) + (m + 1) h) bytes with m the minimiser: for the
+    adjoint workload (N = 2^20, 20000 steps, B = 256, at most 64 cycles between checkpoints) 349
+    states, under 4 GiB; none for heat."""
+    sw = cuda_lib
+    n = 1 << 20
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, KS_PRM, sw.SWEPT_F64, 256)
+    b = sw.swept_adjoint_scratch(plan, 20000, 64)
+    assert b == 349 * 8 * n and b < 4 * 2 ** 30
+    assert sw.swept_adjoint_scratch(plan, 0, 64) == 0
+    assert sw.swept_adjoint_scratch(plan, 20, 64) == (1 + 2 * 64) * 8 * n       # q = 0: rem levels only
+    heat = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [0.25], sw.SWEPT_F64, 256)
+    assert sw.swept_adjoint_scratch(heat, 20000, 64) == 0
+    plan.destroy()
+    heat.destroy()
+
+
+def test_ks_adjoint_2p22_runs_and_matches_fd(cuda_lib):
+    """N = 2^22 (four times the adjoint workload's field), 2000 steps: the gradient fits and
+    agrees with central differences along two directions within 1e-6."""
+    import torch
+    sw = cuda_lib
+    n, nsteps = 1 << 22, 2000
+    u0 = workloads.ks_smoothed(n, 23)
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS, KS_PRM, sw.SWEPT_F64, 256)
+    J = _J_factory(sw, plan, nsteps)
+    _, uT = J(u0)
+    g = sw.swept_adjoint(plan, dev(u0), uT, nsteps, 64)
+    torch.cuda.synchronize()
+    assert sw.swept_adjoint_scratch(plan, nsteps, 64) < 6 * 2 ** 30
+    g = g.cpu().numpy()
+    for d in range(2):
+        v = workloads.fd_direction(n, d)
+        eps = 1e-6
+        fd = (J(u0 + eps * v)[0] - J(u0 - eps * v)[0]) / (2 * eps)
+        ad = math.fsum(g * v)
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (d, fd, ad)
+    plan.destroy()
+
+
 def test_heat_adjoint_is_forward_2n(cuda_lib):
     """Heat: grad of 1/2 sum u(T)^2 = A^(2n) u0 (A symmetric), bit for bit."""
     sw = cuda_lib
