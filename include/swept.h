@@ -256,6 +256,40 @@ int swept_plan_status(swept_plan_t plan, void *stream);
  */
 int swept_plan_last_advance(swept_plan_t plan, int64_t *launches, int64_t *ring_launches, double *ring_ms);
 
+/* ---- one stage at a time (a slice of a problem sharded over nodes) ------ */
+
+/*
+ * swept_stage -- stage k of swept_advance's schedule on every window of the
+ * plan: a V-fill of height hv from the leading edges of stage k-1, then a
+ * trapezoid of height ht whose leading edges it writes (Section 3, one
+ * stage of every node; swept_advance is the sequence stage(0, 0, h),
+ * stage(k, h, h) for k = 1..q-1, stage(q, h, rem), stage(q+1, rem, 0) for
+ * nsteps = q*h + rem > h, and stage(0, 0, rem), stage(1, rem, 0) below h).
+ * Windows are shifted by B/2 when k is odd; the windows wrap around the
+ * plan's N points, so a plan over one node's slice of a larger periodic
+ * problem computes every window inside the slice exactly, and the one window
+ * that straddles the slice's end reads the edge half that swept_edge_copy
+ * put into its neighbour slot (the exchange of Section 3).  hv = 0 loads the
+ * flat state from u; ht = 0 stores the filled level to u, as do the top of a
+ * partial trapezoid (ht < h) and the gap of a partial fill.
+ *   u   device state of the plan's layout.
+ *   k   >= 0; hv, ht in [0, h], not both 0.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOTSUP (uneven tiles), SWEPT_ECUDA.
+ */
+int swept_stage(swept_plan_t plan, void *u, int64_t k, int hv, int ht, void *stream);
+
+/*
+ * swept_edge_copy -- copy one window's leading-edge half of stage k's edge
+ * buffer (the message a node sends after a stage, Section 3): side 0 is the
+ * left edges L[h][2r], side 1 the right edges R[h][2r], B edge elements of the
+ * plan's edge element size (8 bytes for FP64 and F32C (hi, lo) pairs, 4 for
+ * F32, 16 for the Runge-Kutta pairs, 72 / 48 for Euler point states), level
+ * by level.  dir 0: from the plan into buf; dir 1: from buf into the plan.
+ *   buf  device memory of B edge elements.
+ * Errors: SWEPT_EINVAL (window, side, dir, pointers; uneven tiles), SWEPT_ECUDA.
+ */
+int swept_edge_copy(swept_plan_t plan, int64_t k, int window, int side, void *buf, int dir, void *stream);
+
 /* ---- adjoint ----------------------------------------------------------- */
 
 /*

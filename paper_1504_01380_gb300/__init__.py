@@ -36,6 +36,7 @@ EXPORTS = (
     "swept_batch_plan", "swept_batch_set", "swept_batch_info", "swept_advance_batch",
     "swept_batch_status", "swept_batch_destroy", "swept_adjoint", "swept_batch_naive_advance",
     "swept_plan_status", "swept_plan_last_advance", "swept_probe_alu", "swept_adjoint_scratch",
+    "swept_stage", "swept_edge_copy",
 )
 
 SWEPT_BOPT_TIMEOUT_S, SWEPT_BOPT_DROP_ITEM, SWEPT_BOPT_GRID, SWEPT_BOPT_GRAPH, SWEPT_BOPT_RUN_LEN = 0, 1, 2, 3, 4
@@ -110,6 +111,10 @@ def load(path: str | None = None):
         L.swept_batch_destroy.restype = None
         L.swept_adjoint.argtypes = [vp, vp, vp, vp, i64, i32, vp]
         L.swept_adjoint.restype = i32
+        L.swept_stage.argtypes = [vp, vp, i64, i32, i32, vp]
+        L.swept_stage.restype = i32
+        L.swept_edge_copy.argtypes = [vp, i64, i32, i32, vp, i32, vp]
+        L.swept_edge_copy.restype = i32
         L.swept_adjoint_scratch.argtypes = [vp, i64, i32, ctypes.POINTER(i64)]
         L.swept_adjoint_scratch.restype = i32
         L.swept_probe_alu.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), vp]
@@ -230,6 +235,31 @@ def swept_plan_last_advance(plan: Plan):
     _check(load().swept_plan_last_advance(plan.handle, ctypes.byref(n), ctypes.byref(nr), ctypes.byref(ms)),
            "swept_plan_last_advance")
     return int(n.value), int(nr.value), float(ms.value)
+
+
+def swept_stage(plan: Plan, u, k: int, hv: int, ht: int, stream=None):
+    """Stage k of the swept schedule (V-fill hv, then trapezoid ht) on every window of the plan."""
+    _check(load().swept_stage(plan.handle, _dev_ptr(u, plan.state_bytes, "u"), int(k), int(hv), int(ht),
+                              _stream(stream)), "swept_stage")
+    return u
+
+
+def edge_element_bytes(plan: Plan) -> int:
+    """Bytes of one leading-edge element of the plan (what swept_edge_copy moves B of)."""
+    if plan.stencil == SWEPT_EULER:
+        return 72 if plan.dtype == SWEPT_F64 else 48
+    if plan.stencil in (SWEPT_HEAT_RK2, SWEPT_KS_RK2):
+        return 16
+    return 4 if plan.dtype == SWEPT_F32 else 8
+
+
+def swept_edge_copy(plan: Plan, k: int, window: int, side: int, buf, to_plan: bool, stream=None):
+    """Copy window's left (side 0) or right (side 1) edge half of stage k's edge buffer into buf,
+    or (to_plan) from buf into the plan."""
+    _check(load().swept_edge_copy(plan.handle, int(k), int(window), int(side),
+                                  _dev_ptr(buf, plan.B * edge_element_bytes(plan), "buf"), 1 if to_plan else 0,
+                                  _stream(stream)), "swept_edge_copy")
+    return buf
 
 
 def swept_naive_advance(plan: Plan, u, nsteps: int, stream=None):

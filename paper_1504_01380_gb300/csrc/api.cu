@@ -867,6 +867,45 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
   return cuda_status(e);
 }
 
+int swept_stage(swept_plan_t p, void* u, int64_t k, int hv, int ht, void* stream) {
+  if (!p || !u || k < 0 || !aligned16(u)) return SWEPT_EINVAL;
+  if (hv < 0 || ht < 0 || hv > p->H || ht > p->H || (hv == 0 && ht == 0)) return SWEPT_EINVAL;
+  if (p->nreg != p->nwin) return SWEPT_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!swept::call_on_device(p->device, s, {u})) return SWEPT_EINVAL;
+  // the same stage as swept_advance's stage k: windows shifted by B/2 when k
+  // is odd, edges of stage k-1 in buffer (k+1) & 1, its own in buffer k & 1
+  unsigned char* buf[2] = {p->edges, p->edges + p->edge_half};
+  StageArgs a{};
+  a.u = u;
+  a.N = p->N;
+  a.nwin = p->nwin;
+  a.c = p->c;
+  a.pdl = p->pdl;
+  a.offset = (k & 1) ? p->B / 2 : 0;
+  a.hv = hv;
+  a.ht = ht;
+  a.ein = buf[(k + 1) & 1];
+  a.eout = buf[k & 1];
+  a.lev_fill = k >= 1 ? (k - 1) * p->H : 0;
+  a.lev_trap = k * p->H;
+  const bool full = use_ring(p) && hv == p->H && ht == p->H;
+  return cuda_status(full ? launch_ring(p, a, s) : launch_stage(p, a, s));
+}
+
+int swept_edge_copy(swept_plan_t p, int64_t k, int window, int side, void* buf, int dir, void* stream) {
+  if (!p || !buf || k < 0 || window < 0 || window >= p->nwin || (side != 0 && side != 1)) return SWEPT_EINVAL;
+  if ((dir != 0 && dir != 1) || p->nreg != p->nwin) return SWEPT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!swept::call_on_device(p->device, s, {buf})) return SWEPT_EINVAL;
+  // one window's slot is 2B elements: B of left edges (h levels x 2r), then B of right edges
+  const size_t half = p->edge_half / ((size_t)p->nwin * 2);
+  unsigned char* e = p->edges + (size_t)(k & 1) * p->edge_half + ((size_t)window * 2 + side) * half;
+  cudaError_t r = dir == 0 ? cudaMemcpyAsync(buf, e, half, cudaMemcpyDeviceToDevice, s)
+                           : cudaMemcpyAsync(e, buf, half, cudaMemcpyDeviceToDevice, s);
+  return cuda_status(r);
+}
+
 int swept_plan_last_advance(swept_plan_t p, int64_t* launches, int64_t* ring_launches, double* ring_ms) {
   if (!p || !launches || !ring_launches || !ring_ms) return SWEPT_EINVAL;
   *launches = p->last_launches;
