@@ -110,10 +110,12 @@ typedef struct swept_plan_s *swept_plan_t;
  * into N/B tiles of B points, each advanced by the stencil `stencil_id`
  * (radius `radius`, parameters `params[0..nparams)`) in arithmetic `dtype`.
  *   N       >= B, N % B == 0; or (K <= 16; Euler equations K <= 4 in FP64,
- *           8 compensated) any N that is a multiple of 32*radius and at
- *           least (N mod B)/(32 radius) tiles long: the last (N mod B)/(32
- *           radius) windows are then B + 32 radius wide (uneven tiles: their
- *           trapezoids keep the height h, their Vs stay B wide).
+ *           8 compensated) any N at least nwide = ceil((N mod B)/(32 radius))
+ *           tiles long: the last nwide windows are then wider than B (uneven
+ *           tiles: their trapezoids keep the height h, their Vs stay B wide),
+ *           all B + 32 radius points but the last, which takes the rest
+ *           (B + 1 .. B + 32 radius points).  With B = 0 any N >= 32 (heat,
+ *           Euler equations) or >= 64 (KS) is tiled.
  *           swept_adjoint does not take uneven plans.
  *   radius  must equal the stencil's radius (1 heat, 2 KS, either time
  *           integrator; 1 Euler equations).

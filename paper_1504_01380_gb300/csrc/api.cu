@@ -143,19 +143,20 @@ bool use_ring(const swept_plan_s* p) {
 // Default tile width: the largest of 512, 256, ... that keeps K a multiple
 // of the radius and divides N, or else tiles it with uneven tiles (Euler
 // equations: from 64 in FP64, 128 in F32C).
-// Uneven tiles: N = nreg*B + nwide*(B + 32r) with nwide = (N mod B) / (32r)
-// and nreg >= 0, for every stencil and precision the plan takes with K <= 16
-// (Euler equations: K <= 4 in FP64, 8 compensated).  Returns nreg, or -1
-// when N cannot be tiled so.
+// Uneven tiles: N = nreg*B + (nwide - 1)*(B + 32r) + W with
+// nwide = ceil((N mod B) / (32r)) and the last window W = N - (its start)
+// points wide (B + 1 .. B + 32r), nreg >= 0, for every stencil and precision
+// the plan takes with K <= 16 (Euler equations: K <= 4 in FP64, 8
+// compensated).  Any N of at least nwide tiles is tiled so.  Returns nreg, or
+// -1 when N cannot be tiled so.
 int64_t uneven_nreg(int64_t N, int B, int radius, int stencil, int dtype) {
   if (stencil == SWEPT_EULER) {
     if (B / 32 > (dtype == SWEPT_F64 ? 4 : 8)) return -1;
   } else if (B / 32 > 16) {
     return -1;
   }
-  if (N % (32 * radius)) return -1;
   const int64_t extra = N % B;
-  const int64_t nwide = extra / (32 * radius);
+  const int64_t nwide = (extra + 32 * radius - 1) / (32 * radius);
   const int64_t nreg = N / B - nwide;
   return nreg >= 0 && nreg + nwide >= 1 ? nreg : -1;
 }
@@ -226,7 +227,7 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->B = B;
   p->K = K;
   p->H = B / (2 * rad);
-  p->nwin = (int)(nreg + (N - nreg * B) / (B + 32 * rad));
+  p->nwin = (int)(N / B);                 // nreg regular windows, then the wide ones
   p->nreg = (int)nreg;
   for (int i = 0; i < 3; ++i) p->prm[i] = i < nparams ? params[i] : 0.0;
   p->c = c;

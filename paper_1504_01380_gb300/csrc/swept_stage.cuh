@@ -114,8 +114,8 @@ struct StageImpl {
   }
 
   // Capture for trapezoid level m = P*L + J: left edge at positions
-  // P*K + R*J + q, right edge at (31 - P)*K + K - R*J - 2R + q.
-  template <int J>
+  // P*K + R*J + q, right edge (when RIGHT) at (31 - P)*K + K - R*J - 2R + q.
+  template <int J, bool RIGHT = true>
   static __device__ __forceinline__ void capture(const Tile<DT, K>& t, E* oL, E* oR, int m, int P,
                                                  int lane) {
 #pragma unroll
@@ -125,12 +125,32 @@ struct StageImpl {
       const int k = cc - dl * K;
       if (lane == P + dl) oL[m * 2 * R + q] = t.get(k);
     }
+    if constexpr (RIGHT) {
+#pragma unroll
+      for (int q = 0; q < 2 * R; ++q) {
+        const int cc = K - R * J - 2 * R + q;
+        const int dr = cc < 0 ? 1 : 0;
+        const int k = cc + dr * K;
+        if (lane == 31 - P - dr) oR[m * 2 * R + q] = t.get(k);
+      }
+    }
+  }
+
+  // Right edge of level m of a trapezoid over `width` points (fewer than the
+  // tile's 32K: the last window of a tiling of any N): positions
+  // width - r m - 2r + q, whose lane and register are known only at run time.
+  static __device__ __forceinline__ void capture_right_at(const Tile<DT, K>& t, E* oR, int m, int width,
+                                                          int lane) {
 #pragma unroll
     for (int q = 0; q < 2 * R; ++q) {
-      const int cc = K - R * J - 2 * R + q;
-      const int dr = cc < 0 ? 1 : 0;
-      const int k = cc + dr * K;
-      if (lane == 31 - P - dr) oR[m * 2 * R + q] = t.get(k);
+      const int pos = width - R * m - 2 * R + q;
+      const int pl = pos / K;
+      const int pk = pos - pl * K;
+      E v = t.get(0);
+#pragma unroll
+      for (int k = 1; k < K; ++k)
+        if (pk == k) v = t.get(k);
+      if (lane == pl) oR[m * 2 * R + q] = v;
     }
   }
 
@@ -203,9 +223,11 @@ struct StageImpl {
 
   // Levels 1..ht of the shrinking triangle; edges of levels 0..ht-1 go to
   // oL / oR.  On return the tile holds level ht-1 (the caller computes the
-  // top level when ht < h).
+  // top level when ht < h).  GEN: the trapezoid spans `width` points, its
+  // right edges found at run time.
+  template <bool GEN = false>
   static __device__ __forceinline__ void trapezoid(Tile<DT, K>& t, E* oL, E* oR, int ht, int lane,
-                                                   const StageArgs& a, int64_t ws) {
+                                                   const StageArgs& a, int64_t ws, int width = B) {
     const Consts& c = a.c;
     Coef cf;
 #pragma unroll 1
@@ -216,7 +238,9 @@ struct StageImpl {
       }
       const int P = m / L;
       const int j = m - P * L;
-      select<0, L>(j, [&](auto J) { capture<decltype(J)::value>(t, oL, oR, m, P, lane); });
+      select<0, L>(j, [&](auto J) { capture<decltype(J)::value, !GEN>(t, oL, oR, m, P, lane); });
+      if constexpr (GEN) capture_right_at(t, oR, m, width, lane);
+      else (void)width;
     }
   }
 
@@ -248,9 +272,12 @@ struct StageImpl {
   // right edges of window wl and the left edges of window wr, edges out to
   // window wo's slot; edge slots of 2*eslot elements.  wrap_points: the
   // periodic wrap may fall inside a lane's K points (uneven tiles), so the
-  // flat state is loaded point by point.
+  // flat state is loaded point by point.  GEN: a trapezoid of `width` <= B
+  // points (the last window of a tiling of any N; the lanes' points past it
+  // are loaded but never computable, captured or stored).
+  template <bool GEN = false>
   static __device__ void run_window_at(const StageArgs& a, E* sm, int64_t ws, int wl, int wr, int wo, int eslot,
-                                       bool wrap_points) {
+                                       bool wrap_points, int width = B) {
     const int lane = threadIdx.x & 31;
     const int64_t N = a.N;
     E* sL = sm;
@@ -291,7 +318,7 @@ struct StageImpl {
       }
     }
     if (a.ht > 0) {
-      trapezoid(t, sL, sR, a.ht, lane, a, ws);
+      trapezoid<GEN>(t, sL, sR, a.ht, lane, a, ws, width);
       __syncwarp();
       E* eout = static_cast<E*>(a.eout) + (int64_t)wo * (2 * eslot);
       warp_copy(eout, sL, a.ht * 2 * R, lane);
@@ -301,7 +328,7 @@ struct StageImpl {
         Coef cf;
         load_coef(cf, a, ws, lane, a.lev_trap + a.ht);
         tile_level<ST, DT, K, false>(t, a.c, lane, nullptr, nullptr, cf.u, cf.sub);
-        const int lo = R * a.ht, hi = B - R * a.ht;
+        const int lo = R * a.ht, hi = (GEN ? width : B) - R * a.ht;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           const int x = lane * K + k;

@@ -1,5 +1,6 @@
 // Uneven tiles (N not a multiple of the tile width B): the swept stages with
-// the last windows B + 32r wide.  Every V between two tiles stays exactly B
+// the last windows wider than B: all B + 32r wide but the very last, which
+// takes what is left (B + 1 .. B + 32r points).  Every V between two tiles stays exactly B
 // wide (Section 3's V grows by r points per side per level around a tile
 // boundary, whatever the tiles' widths), so a wide window of width W = B +
 // 32r is its V (a regular B window centred on the previous stage's boundary)
@@ -46,7 +47,8 @@ swept_wide_kernel(const StageArgs a, int nreg, int odd) {
     StageArgs at = a;
     at.hv = 0;
     const int64_t ws = odd ? xj + B / 2 : xj;
-    StageImpl<ST, DT, KW>::run_window_at(at, sm, ws, 0, 0, j, B, true);
+    // the last window of a tiling of any N may be narrower than 32 KW points
+    StageImpl<ST, DT, KW>::template run_window_at<true>(at, sm, ws, 0, 0, j, B, true, (int)(xj1 - xj));
   }
 }
 

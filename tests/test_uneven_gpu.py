@@ -48,6 +48,61 @@ def test_uneven_default_tile_for_a_prime_multiple(cuda_lib):
     assert_same(plan, run_gpu(sw, plan, u0, 3000, naive=True), oracle_run(HEAT, F32C, u0, 3000))
 
 
+# Any N: the last wide window takes what is left (B + 1 .. B + 32r points), so N need not be
+# a multiple of 32r.  Primes, N just above one tile, several wide windows with an odd last one.
+ANY_N = [(HEAT, F64, 32, 1009), (HEAT, F32C, 64, 357), (HEAT, F32, 128, 4099), (HEAT, F64, 512, 512 * 3 + 7),
+         (KS, F64, 128, 1009), (KS, F32C, 64, 100), (KS, F32C, 256, 3001), (KS, F32, 64, 65),
+         (HEAT, F32C, 1024 // 2, 32 * 1009 + 7)]
+
+
+@pytest.mark.parametrize("stencil,dtype,B,N", ANY_N)
+def test_any_n_bit_exact(cuda_lib, stencil, dtype, B, N):
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, B)
+    h = plan.h
+    u0 = initial(stencil, N, 7000 + N)
+    for nsteps in sorted({1, h - 1, h, h + 1, 2 * h, 3 * h + h // 2 + 1}):
+        if nsteps >= 1:
+            assert_same(plan, run_gpu(sw, plan, u0, nsteps), oracle_run(stencil, dtype, u0, nsteps))
+
+
+@pytest.mark.parametrize("stencil,N,B", [(HEAT, 1009, 128), (HEAT, 50, 32), (KS, 1009, 128), (KS, 100, 64),
+                                         (HEAT, 32 * 1009 + 7, 512)])
+def test_any_n_default_tile(cuda_lib, stencil, N, B):
+    """B = 0 picks the widest tile that fits N (a prime N, N below twice the smallest tile):
+    swept == oracle and naive == oracle."""
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), F32C, 0)
+    assert plan.B == B
+    u0 = initial(stencil, N, 8000 + N)
+    nsteps = 3 * plan.h + 5
+    want = oracle_run(stencil, F32C, u0, nsteps)
+    assert_same(plan, run_gpu(sw, plan, u0, nsteps), want)
+    assert_same(plan, run_gpu(sw, plan, u0, nsteps, naive=True), want)
+
+
+def test_any_n_runge_kutta_and_euler(cuda_lib):
+    """The last window of any width for the Runge-Kutta pairs and the Euler point states."""
+    import oracle
+    from tests.test_rk2_gpu import prm, initial as rk2_initial, run as rk2_run
+    from tests.test_euler_gpu import state, run as euler_run, oracle_run as euler_oracle, assert_same as euler_same
+    sw = cuda_lib
+    for st, B, N in ((2, 64, 64 * 4 + 33), (3, 128, 128 * 3 + 71)):
+        r = 1 if st == 2 else 2
+        plan = sw.swept_plan(N, r, st, prm(st), F64, B)
+        u0 = rk2_initial(st, N, 9000 + N)
+        for nsteps in (1, plan.h // 2, 3 * (plan.h // 2) + 2):
+            assert np.array_equal(rk2_run(sw, plan, u0, nsteps), oracle.advance_rk2_f64(st, prm(st), u0, nsteps))
+    for dtype, B, N in ((F64, 64, 64 * 3 + 45), (F32C, 128, 128 * 4 + 101)):
+        q, prm_e = state(N, 9100 + N)
+        plan = sw.swept_plan(N, 1, 4, prm_e, dtype, B)
+        per_stage = plan.h // 4
+        for nsteps in (1, per_stage, 3 * per_stage + 1):
+            euler_same(euler_run(sw, plan, q, nsteps), euler_oracle(prm_e, q, nsteps, dtype))
+
+
 def test_uneven_adjoint_not_supported(cuda_lib):
     import torch
     sw = cuda_lib
