@@ -4,10 +4,12 @@
 // writes it once, so the kernel is bound by HBM bandwidth.
 //
 // Each thread owns V = 4 consecutive points (16-byte vector loads of FP32
-// hi/lo, two 16-byte loads of FP64).  The r neighbours beyond a thread's
-// points come from the adjacent lanes by shuffle; lanes at a warp's ends (or
-// next to the end of the array) read them from global memory, which the
-// neighbouring warp's loads have usually brought into L2 already.
+// hi/lo, two 16-byte loads of FP64, when aligned).  The r neighbours beyond a
+// thread's points come from the adjacent lanes by shuffle; lanes at a warp's
+// ends (or within r of the end of the array) read them from global memory,
+// which the neighbouring warp's loads have usually brought into L2 already.
+// When N is not a multiple of V the last thread owns the N mod V points left,
+// loaded and stored one by one, and its right neighbours wrap to the start.
 #include "swept_internal.h"
 
 namespace swept {
@@ -37,9 +39,25 @@ naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N
   const int lane = threadIdx.x & 31;
   const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
   const bool valid = i0 < N;
+  // the last thread of a field whose N is not a multiple of V owns fewer points
+  const int64_t left = N - i0;
+  const bool full = left >= kV;
   Tile<DT, kV> t;
   t.zero();
-  if (valid) load_points<kV>(t, in, N, i0);
+  if (valid) {
+    if (full) {
+      load_points<kV>(t, in, N, i0);
+    } else {
+      Tile<DT, 1> one;
+#pragma unroll
+      for (int k = 0; k < kV; ++k) {
+        if (k < left) {
+          load_points<1>(one, in, N, i0 + k);
+          t.put(k, one.get(0));
+        }
+      }
+    }
+  }
   Cc x[kV + 2 * R];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -57,7 +75,17 @@ naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N
       x[i] = hi_at<DT>(in, g);
     }
   }
-  if (lane == 31 || i0 + kV >= N) {
+  if (!full) {
+    // the points after the tail wrap to the start of the field
+#pragma unroll
+    for (int k = 0; k < kV + R; ++k) {
+      if (k >= left && k < left + R) {
+        int64_t g = i0 + k;
+        if (g >= N) g -= N;
+        x[R + k] = hi_at<DT>(in, g);
+      }
+    }
+  } else if (lane == 31 || i0 + kV + R > N) {
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       int64_t g = i0 + kV + i;
@@ -66,12 +94,18 @@ naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N
     }
   }
   Core<ST, DT, kV>::apply(t, x, c);
-  store_points<kV>(t, out, N, i0);
+  if (full) {
+    store_points<kV>(t, out, N, i0);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kV; ++k)
+      if (k < left) store_point<kV>(t, k, out, N, i0 + k);
+  }
 }
 
 template <int ST, class DT>
 cudaError_t launch(const void* in, void* out, int64_t N, const Consts& c, cudaStream_t s, bool pdl) {
-  const int64_t threads = N / kV;
+  const int64_t threads = (N + kV - 1) / kV;
   const int64_t grid = (threads + kNaiveThreads - 1) / kNaiveThreads;
   return launch_kernel(pdl, naive_step_kernel<ST, DT>, dim3((unsigned)grid), dim3(kNaiveThreads), 0, s, in, out,
                        N, c);
@@ -88,12 +122,24 @@ naive_rk2_kernel(int sub, const double* __restrict__ u, const double* __restrict
   const int lane = threadIdx.x & 31;
   const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
   const bool valid = i0 < N;
+  const int64_t left = N - i0;           // the last thread may own fewer than V points
+  const bool full = left >= kV;
   const double* arg = sub == 0 ? u : m;
   Tile<F64P, kV> t;
   t.zero();
   if (valid) {
-    ld_chunk<kV>(u + i0, t.u);
-    ld_chunk<kV>(arg + i0, t.m);
+    if (full) {
+      ld_chunk<kV>(u + i0, t.u);
+      ld_chunk<kV>(arg + i0, t.m);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kV; ++k) {
+        if (k < left) {
+          t.u[k] = u[i0 + k];
+          t.m[k] = arg[i0 + k];
+        }
+      }
+    }
   }
   double x[kV + 2 * R];
 #pragma unroll
@@ -112,7 +158,16 @@ naive_rk2_kernel(int sub, const double* __restrict__ u, const double* __restrict
       x[i] = arg[g];
     }
   }
-  if (lane == 31 || i0 + kV >= N) {
+  if (!full) {
+#pragma unroll
+    for (int k = 0; k < kV + R; ++k) {
+      if (k >= left && k < left + R) {
+        int64_t g = i0 + k;
+        if (g >= N) g -= N;
+        x[R + k] = arg[g];
+      }
+    }
+  } else if (lane == 31 || i0 + kV + R > N) {
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       int64_t g = i0 + kV + i;
@@ -121,7 +176,14 @@ naive_rk2_kernel(int sub, const double* __restrict__ u, const double* __restrict
     }
   }
   RK2Core<ST, kV>::apply(t, x, c, sub);
-  st_chunk<kV>(out + i0, sub == 0 ? t.m : t.u);
+  const double* res = sub == 0 ? t.m : t.u;
+  if (full) {
+    st_chunk<kV>(out + i0, res);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kV; ++k)
+      if (k < left) out[i0 + k] = res[k];
+  }
 }
 
 // Euler equations, one stage of the midpoint rule per launch (the slopes
@@ -218,8 +280,8 @@ cudaError_t launch_naive_euler_f32c(int full, const float* arg, const float* hi,
 
 cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double* m, double* out, int64_t N,
                              const Consts& c, cudaStream_t s, bool pdl) {
-  if (N % kV) return cudaErrorInvalidValue;
-  const int64_t grid = (N / kV + kNaiveThreads - 1) / kNaiveThreads;
+  if (N <= 0) return cudaErrorInvalidValue;
+  const int64_t grid = ((N + kV - 1) / kV + kNaiveThreads - 1) / kNaiveThreads;
   if (stencil == 2)
     return launch_kernel(pdl, naive_rk2_kernel<kHeatRK2>, dim3((unsigned)grid), dim3(kNaiveThreads), 0, s, sub, u,
                          m, out, N, c);
@@ -229,7 +291,7 @@ cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double
 
 cudaError_t launch_naive_step(int stencil, int dtype, const void* in, void* out, int64_t N,
                               const Consts& c, cudaStream_t s, bool pdl) {
-  if (N % kV) return cudaErrorInvalidValue;
+  if (N <= 0) return cudaErrorInvalidValue;
   if (stencil == kHeat) {
     if (dtype == 2) return launch<kHeat, F32>(in, out, N, c, s, pdl);
     return dtype == 0 ? launch<kHeat, F64>(in, out, N, c, s, pdl) : launch<kHeat, F32C>(in, out, N, c, s, pdl);
