@@ -710,15 +710,16 @@ def cpu_leg_latency(u0, nsteps, got):
 def report_ks_c2(peaks, flush):
     """KS (forward Euler), N = 2^22, dx = 0.5, dt = 0.002, 50000 steps, u0 = 0.1 smooth^10(N(0,1)).
 
-    Compensated FP32 (B = 512, streamed ring) over the full 50000 steps against the naive
-    stepper; FP64 swept and naive over 5000 steps (both FP64-pipe-bound).  Error: the
+    Compensated FP32 (B = 1024, streamed ring; B = 512 beside it) over the full 50000 steps
+    against the naive stepper; FP64 swept (B = 1024) and naive over 5000 steps (both
+    FP64-pipe-bound).  Error: the
     compensated state after 2000 steps against the FP64 oracle (after 50000 steps the chaotic
     dynamics have amplified rounding differences to the size of the solution); the FP64 GPU
     state after 2000 steps must equal the oracle's bit for bit.
     """
     import torch
     import paper_1504_01380_gb300 as sw
-    n, nsteps, nshort, nerr, B = 1 << 22, 50000, 5000, 2000, 512
+    n, nsteps, nshort, nerr, B = 1 << 22, 50000, 5000, 2000, 1024
     prm = [workloads.KS_DT, workloads.KS_DX]
     u0 = workloads.ks_smoothed(n)
     u64 = torch.tensor(u0, device="cuda")
@@ -730,6 +731,11 @@ def report_ks_c2(peaks, flush):
         flush.fill_(1)
         return cuda_time(fn)
 
+    sweep = {}
+    p512 = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F32C, 512)
+    run(lambda: sw.swept_advance(p512, u, nerr), u, u32)
+    sweep["512"] = n * nsteps / run(lambda: sw.swept_advance(p512, u, nsteps), u, u32)
+    p512.destroy()
     plan = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F32C, B)
     sw.swept_plan_set(plan, sw.SWEPT_OPT_TIME_RING, 1)
     run(lambda: sw.swept_advance(plan, u, nerr), u, u32)                      # warm-up
@@ -740,7 +746,7 @@ def report_ks_c2(peaks, flush):
     t_nv = run(lambda: sw.swept_naive_advance(plan, u, nshort), u, u32)
     plan.destroy()
     v = u64.clone()
-    p64 = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F64, 256)
+    p64 = sw.swept_plan(n, 2, sw.SWEPT_KS, prm, sw.SWEPT_F64, B)
     t64 = run(lambda: sw.swept_advance(p64, v, nshort), v, u64)
     t64n = run(lambda: sw.swept_naive_advance(p64, v, nshort), v, u64)
     run(lambda: sw.swept_advance(p64, v, nerr), v, u64)
@@ -753,7 +759,8 @@ def report_ks_c2(peaks, flush):
     peak, unit, source, _ = peak_block(peaks, "fp32")
     leg["gpu_f64_bit_exact"] = bool(np.array_equal(f64_2000, want))
     rate = n * nsteps / t
-    return {"workload": f"ks1d_N{n}_dx0.5_dt0.002_{nsteps}steps_f32c_B{B}", "unit": UNIT,
+    sweep[str(B)] = rate
+    return {"workload": f"ks1d_N{n}_dx0.5_dt0.002_{nsteps}steps_f32c_B{B}", "unit": UNIT, "tile_sweep": sweep,
             "swept": rate, "naive": n * nshort / t_nv, "swept_over_naive": rate / (n * nshort / t_nv),
             "naive_hbm_roof_16B": measured_hbm_gbs() * 1e9 / 16,
             "f64": {"swept": n * nshort / t64, "naive": n * nshort / t64n, "steps": nshort},
@@ -761,7 +768,7 @@ def report_ks_c2(peaks, flush):
             "error_reference": "FP64 oracle after 2000 steps, relative to its max|u|; bar 1e-5",
             "launches": n_all,
             "roofline": roofline(ALGO_OPS_F32C["ks"] * ring_updates / (ring_ms / 1e3), peak, unit, source,
-                                 kernel="swept_stream_kernel<ks,f32c,K=16>", avg_launch_ms=ring_ms / max(1, n_ring),
+                                 kernel="swept_stream_kernel<ks,f32c,K=32>", avg_launch_ms=ring_ms / max(1, n_ring),
                                  ops_per_update=ALGO_OPS_F32C["ks"], executed_ops_per_update=EXEC_OPS_F32C["ks"],
                                  frac_executed=EXEC_OPS_F32C["ks"] * ring_updates / (ring_ms / 1e3) / peak
                                  if peak else None,

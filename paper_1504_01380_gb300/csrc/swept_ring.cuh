@@ -521,8 +521,18 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
       if (resident > 4 * sms) resident = 4 * sms;
       per_sm = per_sm_ring = 1;
     }
+    const bool automatic = nwarps <= 0;
     if (nwarps <= 0 || nwarps > resident) nwarps = resident;
     if (nwarps > nw / 3) nwarps = nw / 3;
+    if (automatic && nwarps >= sms * kWarpsPerBlock) {
+      // Every SM gets the same number of blocks.  The warps wait on their
+      // neighbours once per stage, so the launch runs at the pace of its most
+      // crowded SM: measured on GB300 (KS, compensated FP32, N = 2^22,
+      // B = 1024, at most 3 blocks per SM), 1365 warps (342 blocks: some SMs
+      // 3, some 2) 1.05e12 cell-updates/s, 912 warps (1.5 blocks per SM)
+      // 1.05e12, 1216 warps (2 per SM) 1.30e12.
+      nwarps -= nwarps % (sms * kWarpsPerBlock);
+    }
     if (nwarps < 1 || a.nlaunch) return cudaErrorInvalidValue;
     if (a.stream_query) {
       // Streaming saves each run's extra slot per stage, 1/n of the work for
