@@ -116,7 +116,6 @@ typedef struct swept_plan_s *swept_plan_t;
  *           all B + 32 radius points but the last, which takes the rest
  *           (B + 1 .. B + 32 radius points).  With B = 0 any N >= 32 (heat,
  *           Euler equations) or >= 64 (KS) is tiled.
- *           swept_adjoint does not take uneven plans.
  *   radius  must equal the stencil's radius (1 heat, 2 KS, either time
  *           integrator; 1 Euler equations).
  *   B       tile width: 32*K points with K in {1,2,4,8,16,32}, K % radius
@@ -312,7 +311,7 @@ int swept_edge_copy(swept_plan_t plan, int64_t k, int window, int side, void *bu
  * stepping into a ring of m + 1 chunks of h levels, from which each
  * transposed stage reads its 2h levels.  m is at most 2*K_cycles stages
  * (K_cycles swept cycles of two stages; <= 0 means 64) and is the value that
- * minimises the scratch.  FP64 plans on even tiles only.
+ * minimises the scratch.  FP64 plans, even or uneven tiles.
  *   u0, lambda_T, grad_u0  device double[N]; grad_u0 may not alias u0.
  * Scratch (plan-owned, grown on demand, kept until swept_destroy), for KS
  * with nsteps = q*h + rem:
@@ -320,8 +319,8 @@ int swept_edge_copy(swept_plan_t plan, int64_t k, int window, int side, void *bu
  * (swept_adjoint_scratch returns it; N = 2^20, 20000 steps, h = 64: m = 2,
  * 349 states, 2.9 GB); none for heat.
  * Errors: SWEPT_EINVAL (null or misaligned pointers, grad_u0 == u0, memory of
- * another device), SWEPT_ENOTSUP (F32C, F32, Runge-Kutta, Euler or uneven
- * plan), SWEPT_ENOMEM (the scratch does not fit), SWEPT_ECUDA.
+ * another device), SWEPT_ENOTSUP (F32C, F32, Runge-Kutta or Euler plan),
+ * SWEPT_ENOMEM (the scratch does not fit), SWEPT_ECUDA.
  */
 int swept_adjoint(swept_plan_t plan, const void *u0, const void *lambda_T, void *grad_u0,
                   int64_t nsteps, int K_cycles, void *stream);

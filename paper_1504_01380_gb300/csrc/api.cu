@@ -727,11 +727,18 @@ int adjoint_ks(swept_plan_s* p, const double* u0, double* lam, int64_t F, const 
     a.eout = buf[k & 1];
     a.lev_fill = k >= 1 ? (k - 1) * H : 0;
     a.lev_trap = k * H;
-    if (use_ring(p) && hv == p->H && ht == p->H) {
-      const int w = (p->diamond == SWEPT_DIAMOND_AUTO && p->ring_warps == 0) ? -1 : p->ring_warps;
-      return swept::launch_ring_ksadj_f64(p->K, a, w, s);
+    const bool full = use_ring(p) && p->nreg > 0 && hv == p->H && ht == p->H;
+    const int w = (p->diamond == SWEPT_DIAMOND_AUTO && p->ring_warps == 0) ? -1 : p->ring_warps;
+    if (p->nreg == p->nwin)
+      return full ? swept::launch_ring_ksadj_f64(p->K, a, w, s) : swept::launch_stage_ksadj_f64(p->K, a, s);
+    // uneven tiles: the regular windows, then the wide ones
+    if (p->nreg > 0) {
+      a.nlaunch = p->nreg;
+      r = full ? swept::launch_ring_ksadj_f64(p->K, a, w, s) : swept::launch_stage_ksadj_f64(p->K, a, s);
+      a.nlaunch = 0;
     }
-    return swept::launch_stage_ksadj_f64(p->K, a, s);
+    if (r == cudaSuccess) r = swept::launch_wide_ksadj(p->K, a, p->nreg, (int)(k & 1), s);
+    return r;
   };
   const int64_t q = L.q;
   const int rem = (int)L.rem;
@@ -753,7 +760,7 @@ extern "C" {
 
 int swept_adjoint_scratch(swept_plan_t p, int64_t nsteps, int K_cycles, int64_t* bytes) {
   if (!p || !bytes || nsteps < 0) return SWEPT_EINVAL;
-  if (p->dtype != SWEPT_F64 || p->subs > 1 || p->nreg != p->nwin) return SWEPT_ENOTSUP;
+  if (p->dtype != SWEPT_F64 || p->subs > 1) return SWEPT_ENOTSUP;
   *bytes = 0;
   if (p->stencil == SWEPT_KS && nsteps > 0)
     *bytes = adjoint_layout(p, nsteps, K_cycles).states * p->N * (int64_t)sizeof(double);
@@ -764,7 +771,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
                   int K_cycles, void* stream) {
   if (!p || !u0 || !lam_T || !grad || nsteps < 0) return SWEPT_EINVAL;
   if (!aligned16(u0) || !aligned16(lam_T) || !aligned16(grad)) return SWEPT_EINVAL;
-  if (p->dtype != SWEPT_F64 || p->subs > 1 || p->nreg != p->nwin) return SWEPT_ENOTSUP;
+  if (p->dtype != SWEPT_F64 || p->subs > 1) return SWEPT_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   if (!swept::call_on_device(p->device, s, {u0, lam_T, grad})) return SWEPT_EINVAL;
   if (u0 == grad) return SWEPT_EINVAL;

@@ -206,6 +206,8 @@ cudaError_t launch_wide_f32c(int stencil, int K, const StageArgs& a, int nreg, i
 cudaError_t launch_wide_f32(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 cudaError_t launch_wide_rk2(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 cudaError_t launch_wide_euler(int dtype, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
+// The transposed KS step (adjoint sweeps) on the wide windows, FP64, K in {2, 4, 8, 16}.
+cudaError_t launch_wide_ksadj(int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 
 // Persistent advance (every stage in one launch, windows synchronised by
 // flags): heat and KS, dtype 0 F64 / 1 F32C / 2 F32, K in {1, 2, 4, 8}.

@@ -69,7 +69,17 @@ struct StageImpl {
     if constexpr (ST == kKSAdj) {
       int64_t g = ws + (int64_t)lane * K;
       if (g >= a.N) g -= a.N;
-      ld_chunk<K>(tape_level(a, a.tape_len - tau) + g, cf.u);
+      const double* lv = tape_level(a, a.tape_len - tau);
+      if (g + K <= a.N) {
+        ld_chunk<K>(lv + g, cf.u);
+      } else {                        // the periodic wrap falls inside this lane's points
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          int64_t gk = g + k;
+          while (gk >= a.N) gk -= a.N;
+          cf.u[k] = lv[gk];
+        }
+      }
     } else if constexpr (Subs<ST>::value > 1) {
       cf.sub = (int)((tau - 1) & (Subs<ST>::value - 1));
       (void)a; (void)ws; (void)lane;
@@ -297,6 +307,22 @@ struct StageImpl {
           if (gk >= N) gk -= N;
           load_points<1>(one, a.u, N, gk);
           t.put(k, one.get(0));
+        }
+      }
+      if constexpr (GEN && DumpsCkpt<ST, DT>::value) {
+        // the wide window's flat base level (its V part stored the middle,
+        // the previous stage its top) is the forward pass's checkpoint when
+        // its stage is one; eslot is the regular tile width
+        if (double* ck = ckpt_of(a, a.lev_trap / (eslot / (2 * R)))) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int x = lane * K + k;
+            if (x < width) {
+              int64_t gx = ws + x;
+              if (gx >= N) gx -= N;
+              ck[gx] = t.get(k);
+            }
+          }
         }
       }
     } else {

@@ -103,59 +103,25 @@ def test_any_n_runge_kutta_and_euler(cuda_lib):
             euler_same(euler_run(sw, plan, q, nsteps), euler_oracle(prm_e, q, nsteps, dtype))
 
 
-def test_uneven_adjoint_not_supported(cuda_lib):
+@pytest.mark.parametrize("N,B,ring", [(128 + 192, 128, False), (1009, 128, False), (20 * 128 + 3 * 192 + 77, 128, True),
+                                      (13 * 256 + 101, 256, True), (64 * 40 + 31, 64, False)])
+def test_uneven_adjoint_matches_oracle(cuda_lib, N, B, ring):
+    """The KS adjoint on uneven tiles of any N: the forward pass's checkpoints come from the
+    regular windows' kernels and from the wide windows' trapezoid loads, the transposed sweep
+    runs the regular windows (per window or on the ring) and then the wide ones; bit-exact
+    against the oracle's discrete adjoint, for step counts around the stage boundaries."""
+    import oracle
     import torch
     sw = cuda_lib
-    N = 128 + 192                         # one 128-point and one 192-point window
-    plan = sw.swept_plan(N, 2, KS, params_of(KS), F64, 128)
-    z = torch.zeros(N, dtype=torch.float64, device="cuda")
-    with pytest.raises(sw.SweptError) as e:
-        sw.swept_adjoint(plan, z, z, 5)
-    assert e.value.code == sw.SWEPT_ENOTSUP
-
-
-@pytest.mark.parametrize("stencil,dtype,B,warps", [(HEAT, F32C, 128, 3), (HEAT, F64, 64, 0), (KS, F32C, 256, 2),
-                                                   (KS, F64, 128, 0)])
-def test_uneven_with_ring_for_the_regular_windows(cuda_lib, stencil, dtype, B, warps):
-    """The regular windows' full diamonds on the ring kernel (forced; several run lengths), the
-    wide windows alongside."""
-    sw = cuda_lib
-    r = 1 if stencil == HEAT else 2
-    nwide = max(1, (B // (32 * r)) - 1)
-    N = 20 * B + nwide * (B + 32 * r)
-    plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, B)
-    sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
-    sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, warps)
-    u0 = initial(stencil, N, 4000 + B)
-    for nsteps in (4 * plan.h + 3, 6 * plan.h):
-        assert_same(plan, run_gpu(sw, plan, u0, nsteps), oracle_run(stencil, dtype, u0, nsteps))
-
-
-@pytest.mark.parametrize("st,B,nreg,nwide", [(2, 64, 3, 1), (2, 128, 5, 3), (3, 128, 2, 1), (3, 256, 4, 3)])
-def test_uneven_runge_kutta(cuda_lib, st, B, nreg, nwide):
-    """Two-stage Runge-Kutta (heat 2, KS 3) on uneven tiles: bit-exact against the RK2 oracle."""
-    from tests.test_rk2_gpu import prm, initial as rk2_initial, run as rk2_run
-    import oracle
-    sw = cuda_lib
-    r = 1 if st == 2 else 2
-    N = nreg * B + nwide * (B + 32 * r)
-    plan = sw.swept_plan(N, r, st, prm(st), F64, B)
-    u0 = rk2_initial(st, N, 5000 + B)
-    steps_per_stage = plan.h // 2
-    for nsteps in (1, steps_per_stage, 3 * steps_per_stage + 2):
-        got = rk2_run(sw, plan, u0, nsteps)
-        assert np.array_equal(got, oracle.advance_rk2_f64(st, prm(st), u0, nsteps)), nsteps
-
-
-@pytest.mark.parametrize("dtype,B,nreg,nwide", [(F64, 64, 3, 1), (F64, 128, 2, 2), (F32C, 128, 4, 3),
-                                                (F32C, 256, 1, 5)])
-def test_uneven_euler(cuda_lib, dtype, B, nreg, nwide):
-    """Euler equations on uneven tiles: bit-exact against the Euler oracles."""
-    from tests.test_euler_gpu import state, run as euler_run, oracle_run as euler_oracle, assert_same as euler_same
-    sw = cuda_lib
-    N = nreg * B + nwide * (B + 32)
-    q, prm_e = state(N, 6000 + B)
-    plan = sw.swept_plan(N, 1, 4, prm_e, dtype, B)
-    per_stage = plan.h // 4
-    for nsteps in (1, per_stage, 3 * per_stage + 1):
-        euler_same(euler_run(sw, plan, q, nsteps), euler_oracle(prm_e, q, nsteps, dtype))
+    u0 = initial(KS, N, 9500 + N)
+    lam = initial(HEAT, N, 9600 + N)
+    plan = sw.swept_plan(N, 2, KS, params_of(KS), F64, B)
+    if ring:
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, 3)
+    h = plan.h
+    for nsteps, K in ((3 * h + 5, 1), (6 * h, 2), (h - 1, 64), (9 * h + h // 2, 1)):
+        got = sw.swept_adjoint(plan, torch.tensor(u0, device="cuda"), torch.tensor(lam, device="cuda"),
+                               nsteps, K).cpu().numpy()
+        want = oracle.adjoint_f64(KS, params_of(KS), u0, lam, nsteps)
+        assert np.array_equal(got, want), (N, B, nsteps, K, np.flatnonzero(got != want)[:8])
