@@ -83,6 +83,9 @@ NOMINAL_SMS, NOMINAL_FP32_LANES = 152, 128
 HEADLINE_SOURCES = ("swept_ring.cuh", "swept_stage.cuh", "swept_device.cuh", "swept_sync.cuh",
                     "swept_internal.h", "stage_heat_f32c.cu")
 HEADLINE_PROFILE = os.path.join(ROOT, "profiles", "swept_stream_kernel_heat_f32c_K32_N2p24.md")
+KS_SOURCES = ("swept_ring.cuh", "swept_stage.cuh", "swept_device.cuh", "swept_sync.cuh", "swept_internal.h",
+              "stage_ks_f32c.cu")
+KS_PROFILE = os.path.join(ROOT, "profiles", "swept_stream_kernel_ks_f32c_K32_N2p22.md")
 
 
 def workload_config(n_gpus: int):
@@ -520,7 +523,8 @@ def run_gpu(args):
         plan.destroy()
         del u, pristine, host_in, host_out, dev64
         torch.cuda.empty_cache()
-        reports = run_reports(peaks, dev, flush)
+        if args.reports == "all":
+            reports = run_reports(peaks, dev, flush)
     naive_roof = hbm * 1e9 / 16.0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
@@ -759,6 +763,7 @@ def report_ks_c2(peaks, flush):
     peak, unit, source, _ = peak_block(peaks, "fp32")
     leg["gpu_f64_bit_exact"] = bool(np.array_equal(f64_2000, want))
     rate = n * nsteps / t
+    traffic, traffic_note = profile_traffic(KS_PROFILE, KS_SOURCES)
     sweep[str(B)] = rate
     return {"workload": f"ks1d_N{n}_dx0.5_dt0.002_{nsteps}steps_f32c_B{B}", "unit": UNIT, "tile_sweep": sweep,
             "swept": rate, "naive": n * nshort / t_nv, "swept_over_naive": rate / (n * nshort / t_nv),
@@ -769,6 +774,9 @@ def report_ks_c2(peaks, flush):
             "launches": n_all,
             "roofline": roofline(ALGO_OPS_F32C["ks"] * ring_updates / (ring_ms / 1e3), peak, unit, source,
                                  kernel="swept_stream_kernel<ks,f32c,K=32>", avg_launch_ms=ring_ms / max(1, n_ring),
+                                 traffic=traffic, traffic_unit="DRAM bytes per launch (ncu)",
+                                 traffic_note=traffic_note,
+                                 algorithmic_edge_bytes_per_launch=2 * 16 * n * (q - 1),
                                  ops_per_update=ALGO_OPS_F32C["ks"], executed_ops_per_update=EXEC_OPS_F32C["ks"],
                                  frac_executed=EXEC_OPS_F32C["ks"] * ring_updates / (ring_ms / 1e3) / peak
                                  if peak else None,
@@ -1175,6 +1183,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--reports", default="all", choices=["all", "none"],
+                    help="one GPU: the other workloads' reports after the headline (all), or the "
+                         "headline line alone (none; e.g. for a launch list of the headline steps)")
     ap.add_argument("--workload", default="heat",
                     choices=["heat", "ks", "batch", "adjoint", "latency", "heat_f64", "ks_rk2", "euler"],
                     help="heat: the headline line (with every report on one GPU); the others print one "
