@@ -32,7 +32,11 @@ run.  On one GPU the line also carries:
                    ks_c2        Kuramoto-Sivashinsky, N = 2^22, 50000 steps;
                    batch_c3     4096 ragged problems in one persistent launch;
                    adjoint_c4   the KS gradient, N = 2^20, 20000 steps, with 32
-                                finite-difference directions.
+                                finite-difference directions;
+                   ks_rk2_f1    KS by the two-stage Runge-Kutta rule (Section 6's
+                                initial condition), N = 2^22;
+                   euler_f2     the Euler equations (Section 7), N = 2^23 and the
+                                4096-cell latency regime.
 Algorithmic counts follow the hot-path scope's figures: compensated FP32
 heat 11 and KS 22 operations per cell-update against the measured FP32
 instruction rate (an add, mul or fma is one operation); FP64 heat 5 and KS 16
@@ -559,7 +563,8 @@ def run_reports(peaks, dev, flush) -> dict:
     out = {}
     for name, fn in (("heat_c1_f64", report_heat_f64), ("latency_c0", report_latency_c0),
                      ("ks_c2", report_ks_c2), ("batch_c3", report_batch_c3),
-                     ("adjoint_c4", report_adjoint_c4)):
+                     ("adjoint_c4", report_adjoint_c4), ("ks_rk2_f1", report_ks_rk2_f1),
+                     ("euler_f2", report_euler_f2)):
         t0 = time.perf_counter()
         try:
             out[name] = fn(peaks, flush)
@@ -1061,35 +1066,57 @@ def _report_line(name, fn, args):
     return 0
 
 
-def run_ks_rk2_workload(args):
-    """KS by two-stage Runge-Kutta from u = 2cos(19x/128) (the paper's Section 6 scheme), FP64."""
+def report_ks_rk2_f1(peaks, flush):
+    """KS by the two-stage Runge-Kutta midpoint rule (two sub-timesteps with a forwarded variable,
+    Section 2) from the paper's Section 6 initial condition u = 2cos(19x/128), N = 2^22, 2500
+    steps (5000 sub-timesteps), FP64: swept over B in {256, 512, 1024} against the naive stepper;
+    the first 100 steps against the oracle, bit for bit."""
     import torch
     import paper_1504_01380_gb300 as sw
-    n, nsteps = 1 << 22, 2500                      # 5000 sub-timesteps
+    n, nsteps, nchk = 1 << 22, 2500, 100
     prm = [workloads.KS_DT, workloads.KS_DX]
-    u0 = torch.tensor(workloads.ks_cosine(n), device="cuda")
-    res = {}
-    for B in (128, 256, 512):
-        plan = sw.swept_plan(n, 2, sw.SWEPT_KS_RK2, prm, sw.SWEPT_F64, B)
-        u = u0.clone()
-        sw.swept_advance(plan, u, nsteps)
-        ms = []
-        for _ in range(args.steps):
-            u.copy_(u0)
-            ms.append(cuda_time(lambda: sw.swept_advance(plan, u, nsteps)))
-        res[str(B)] = n * nsteps / (sum(ms) / args.steps)
-        plan.destroy()
-    plan = sw.swept_plan(n, 2, sw.SWEPT_KS_RK2, prm, sw.SWEPT_F64, 256)
+    u0h = workloads.ks_cosine(n)
+    u0 = torch.tensor(u0h, device="cuda")
     u = u0.clone()
-    naive = n * nsteps / cuda_time(lambda: sw.swept_naive_advance(plan, u, nsteps))
-    best = max(res, key=res.get)
-    line = {"metric": METRIC, "value": res[best], "unit": UNIT + " (time steps of 2 sub-timesteps)",
-            "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": n * nsteps / res[best] * 1e3,
-            "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ks_rk2_N4194304_2500steps_f64_cos19x128", "B": int(best)},
-            "tile_sweep": res, "naive": naive}
-    print(json.dumps(line), flush=True)
-    return 0
+
+    def run(fn):
+        u.copy_(u0)
+        flush.fill_(1)
+        return cuda_time(fn)
+
+    sweep = {}
+    for B in (256, 512, 1024):
+        plan = sw.swept_plan(n, 2, sw.SWEPT_KS_RK2, prm, sw.SWEPT_F64, B)
+        run(lambda: sw.swept_advance(plan, u, nchk))
+        sweep[str(B)] = n * nsteps / run(lambda: sw.swept_advance(plan, u, nsteps))
+        plan.destroy()
+    best = max(sweep, key=sweep.get)
+    plan = sw.swept_plan(n, 2, sw.SWEPT_KS_RK2, prm, sw.SWEPT_F64, int(best))
+    naive = n * nsteps / run(lambda: sw.swept_naive_advance(plan, u, nsteps))
+    run(lambda: sw.swept_advance(plan, u, nchk))
+    got = u.cpu().numpy()
+    plan.destroy()
+    leg = cpu_leg_rk2(u0h, prm, nchk, got)
+    peak, unit, source, _ = peak_block(peaks, "fp64")
+    flop = 2 * ALGO_FLOP_F64["ks"]                # two KS sub-timesteps per time step
+    return {"workload": f"ks_rk2_N{n}_{nsteps}steps_f64_cos19x128", "unit": UNIT + " (time steps of 2 sub-timesteps)",
+            "swept": sweep[best], "best_B": int(best), "tile_sweep": sweep, "naive": naive,
+            "swept_over_naive": sweep[best] / naive,
+            "roofline": roofline(flop * sweep[best], peak, unit, source, kernel="swept_stream_kernel<ks_rk2,f64>",
+                                 flop_per_step=flop),
+            "cpu_baseline": leg}
+
+
+def cpu_leg_rk2(u0, prm, nsteps, got):
+    """Oracle leg of the Runge-Kutta report: the oracle's first steps on the host cores, timed,
+    compared with the GPU's bit for bit."""
+    import oracle
+    threads = cores_used()
+    t0 = time.perf_counter()
+    want = oracle.advance_rk2_f64(oracle.KS_RK2, prm, u0, nsteps, threads)
+    el = time.perf_counter() - t0
+    return {"kind": "oracle", "cores": threads, "value": u0.size * nsteps / el, "unit": UNIT + " (time steps)",
+            "sample": f"N=2^22, first {nsteps} of 2500 steps, FP64", "gpu_bit_exact": bool(np.array_equal(got, want))}
 
 
 def euler_state(n: int, cfl: float = 0.2):
@@ -1103,16 +1130,16 @@ def euler_state(n: int, cfl: float = 0.2):
     return np.concatenate([rho, np.zeros(n), E]), [cfl * dx, dx, 1.4]
 
 
-def run_euler_workload(args):
+def report_euler_f2(peaks, flush):
     """Euler equations (Section 7): second-order finite volumes, minmod, Roe spectral-radius
     dissipation, midpoint rule (4 sub-timesteps per step), periodic Sod state, gamma 1.4.
 
-    For the compensated FP32 state (binary32 fluxes, TwoSum-compensated update) and for FP64:
-    throughput at N = 2^23 cells (201 MB of FP64 state, larger than L2) over the tile widths,
-    against the naive stepper (two fused launches per step, one face per thread); and the
-    latency regime at N = 4096 cells (the paper's run had about 50 cells on each of 64 ranks):
-    time per sub-timestep, swept (graph-replayed stages) against naive (graph-replayed launches).
-    """
+    For the compensated FP32 state and for FP64: throughput at N = 2^23 cells (201 MB of FP64
+    state, larger than L2) over the tile widths against the naive stepper (two fused launches
+    per step, one face per thread), and the latency regime at N = 4096 cells (the paper's run
+    had about 50 cells on each of 64 ranks): time per sub-timestep, swept (graph-replayed
+    stages) against naive (graph-replayed launches).  The 4096-cell runs are compared with the
+    oracle bit for bit (both precisions), and the compensated state with the FP64 oracle."""
     import torch
     import paper_1504_01380_gb300 as sw
     out = {}
@@ -1135,10 +1162,10 @@ def run_euler_workload(args):
         res = {}
         for B in widths:
             plan = sw.swept_plan(n, 1, sw.SWEPT_EULER, prm, dtype, B)
-            res[str(B)] = n * nsteps / mean_time(lambda: sw.swept_advance(plan, u, nsteps), args.steps)
+            res[str(B)] = n * nsteps / mean_time(lambda: sw.swept_advance(plan, u, nsteps), 2)
             plan.destroy()
         plan = sw.swept_plan(n, 1, sw.SWEPT_EULER, prm, dtype, widths[0])
-        naive = n * nsteps / mean_time(lambda: sw.swept_naive_advance(plan, u, nsteps), args.steps)
+        naive = n * nsteps / mean_time(lambda: sw.swept_naive_advance(plan, u, nsteps), 2)
         plan.destroy()
         # latency regime
         nl, stl = 4096, 500
@@ -1151,6 +1178,10 @@ def run_euler_workload(args):
             plan = sw.swept_plan(nl, 1, sw.SWEPT_EULER, prml, dtype, B)
             sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
             lat[str(B)] = mean_time(lambda: sw.swept_advance(plan, u, stl), 3) / (4 * stl)
+            if B == 32:
+                u.copy_(u0)
+                sw.swept_advance(plan, u, stl)
+                got = u.cpu().numpy()
             plan.destroy()
         plan = sw.swept_plan(nl, 1, sw.SWEPT_EULER, prml, dtype, 32)
         g = torch.cuda.CUDAGraph()
@@ -1161,20 +1192,42 @@ def run_euler_workload(args):
         best = max(res, key=res.get)
         bl = min(lat, key=lat.get)
         out[name] = {"workload": f"euler1d_sod_periodic_N{n}_{nsteps}steps_{name}_gamma1.4_cfl0.2",
-                     "best_B": int(best), "value": res[best], "tile_sweep": res, "naive": naive,
+                     "best_B": int(best), "swept": res[best], "tile_sweep": res, "naive": naive,
                      "swept_over_naive": res[best] / naive,
                      "latency": {"workload": f"euler1d_sod_periodic_N{nl}_{stl}steps_{name}", "best_B": int(bl),
                                  "swept_graph_ns_per_sub": {b: t * 1e9 for b, t in lat.items()},
                                  "naive_graph_ns_per_sub": naive_lat * 1e9,
-                                 "speedup_vs_naive": naive_lat / lat[bl]}}
-    head = out["f32c"]
-    line = {"metric": METRIC, "value": head["value"], "unit": UNIT + " (time steps of 4 sub-timesteps)",
-            "n_gpus": 1, "steps": args.steps, "warmup": 1,
-            "ms_per_step": (1 << 23) * 400 / head["value"] * 1e3,
-            "higher_is_better": True, "scaling": "weak", "dtype": "f32c", "data": "synthetic",
-            "config": {"workload": head["workload"], "B": head["best_B"]}, "f32c": head, "f64": out["f64"]}
-    print(json.dumps(line), flush=True)
-    return 0
+                                 "speedup_vs_naive": naive_lat / lat[bl]},
+                     "cpu_baseline": cpu_leg_euler(ql, prml, stl, got, dtype == sw.SWEPT_F64)}
+    return {"unit": UNIT + " (time steps of 4 sub-timesteps)", **out}
+
+
+def cpu_leg_euler(q_planar, prm, nsteps, got, fp64: bool):
+    """Oracle leg of the Euler report: the oracle (FP64 or compensated FP32) on the 4096-cell
+    latency workload, timed on one core, compared with the GPU's bit for bit; the compensated
+    result's error against the FP64 oracle."""
+    import oracle
+    n = q_planar.size // 3
+    q = q_planar.reshape(3, n).T.copy()                      # (N, 3) rows of (rho, m, E)
+    t0 = time.perf_counter()
+    if fp64:
+        want = oracle.euler_advance(prm, q, nsteps)
+        el = time.perf_counter() - t0
+        exact = bool(np.array_equal(got.reshape(3, n).T, want))
+        err = None
+    else:
+        hi, lo = oracle.split_f32c(q.reshape(-1))
+        whi, wlo = oracle.euler_advance_f32c(prm, hi.reshape(-1, 3), lo.reshape(-1, 3), nsteps)
+        el = time.perf_counter() - t0
+        ghi = got[:3 * n].reshape(3, n).T
+        glo = got[3 * n:].reshape(3, n).T
+        exact = bool(np.array_equal(ghi, whi) and np.array_equal(glo, wlo))
+        w64 = oracle.euler_advance(prm, q, nsteps)
+        val = ghi.astype(np.float64) + glo.astype(np.float64)
+        err = float(np.max(np.abs(val - w64)) / np.max(np.abs(w64)))
+    return {"kind": "oracle", "cores": 1, "value": n * nsteps / el, "unit": "cell-steps/s",
+            "sample": f"the {n}-cell latency workload, {nsteps} steps", "gpu_bit_exact": exact,
+            "max_err_f32c_vs_oracle_f64": err}
 
 
 def main():
@@ -1196,13 +1249,10 @@ def main():
     if args.workload == "batch":
         return run_batch_workload(args)
     reports = {"ks": ("ks_c2", report_ks_c2), "adjoint": ("adjoint_c4", report_adjoint_c4),
-               "latency": ("latency_c0", report_latency_c0), "heat_f64": ("heat_c1_f64", report_heat_f64)}
+               "latency": ("latency_c0", report_latency_c0), "heat_f64": ("heat_c1_f64", report_heat_f64),
+               "ks_rk2": ("ks_rk2_f1", report_ks_rk2_f1), "euler": ("euler_f2", report_euler_f2)}
     if args.workload in reports:
         return _report_line(*reports[args.workload], args)
-    if args.workload == "ks_rk2":
-        return run_ks_rk2_workload(args)
-    if args.workload == "euler":
-        return run_euler_workload(args)
     return run_gpu(args)
 
 
