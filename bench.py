@@ -848,6 +848,19 @@ def report_batch_c3(peaks, flush):
         plan.destroy()
     # oracle leg: a seeded sample of small problems, bit for bit, and the compensated state's error
     leg = cpu_leg_batch(problems, states, batch.offsets, result.cpu().numpy())
+    # KS problems over at most 2000 steps (beyond, the chaotic dynamics amplify rounding
+    # differences to the size of the solution): a sub-batch of six seeded KS problems
+    ks_idx = [i for i, (st, n, _, _) in enumerate(problems) if st == 1 and n <= 16384]
+    ks_pick = sorted(np.random.default_rng(8).choice(ks_idx, 6, replace=False).tolist())
+    sub = [(1, problems[i][1], min(problems[i][2], 2000), problems[i][3]) for i in ks_pick]
+    sb = sw.swept_batch_plan(sub, sw.SWEPT_F32C, choice["B_heat"], choice["B_ks"])
+    spool = torch.zeros(sb.pool_bytes, dtype=torch.uint8, device="cuda")
+    for off, i in zip(sb.offsets, ks_pick):
+        seg = spool[off:off + 8 * len(states[i])].view(torch.float32)
+        sw.swept_f32c_split(torch.tensor(states[i], device="cuda"), out=seg)
+    sw.swept_advance_batch(sb, spool)
+    leg["ks_2000"] = cpu_leg_batch_ks(sub, [states[i] for i in ks_pick], sb.offsets, spool.cpu().numpy())
+    sb.destroy()
     info = batch.info()
     batch.destroy()
     peak, unit, source, _ = peak_block(peaks, "fp32")
@@ -891,6 +904,25 @@ def cpu_leg_batch(problems, states, offsets, pool_bytes: np.ndarray, count: int 
     return {"kind": "oracle", "cores": 1, "value": upd / el, "unit": UNIT,
             "sample": f"{len(pick)} seeded problems of at most 2e8 cell-updates, one thread each",
             "gpu_bit_exact": bool(exact), "max_err_heat_f32c_vs_oracle_f64": worst}
+
+
+def cpu_leg_batch_ks(sub, states, offsets, pool_bytes: np.ndarray):
+    """Oracle leg of the batch report's KS sub-batch (at most 2000 steps each): the compensated
+    result against the compensated oracle bit for bit and against the FP64 oracle (bar 1e-5
+    relative to max|u|)."""
+    import oracle
+    exact, worst = True, 0.0
+    for (st, n, nst, p), u0, off in zip(sub, states, offsets):
+        prm = list(p[:2])
+        hi, lo = oracle.split_f32c(u0)
+        whi, wlo = oracle.advance_f32c(st, prm, hi, lo, nst, 1)
+        seg = pool_bytes[off:off + 8 * n].view(np.float32)
+        exact = exact and np.array_equal(seg[:n], whi) and np.array_equal(seg[n:], wlo)
+        w64 = oracle.advance_f64(st, prm, u0, nst, 1)
+        got = seg[:n].astype(np.float64) + seg[n:].astype(np.float64)
+        worst = max(worst, float(np.max(np.abs(got - w64)) / np.max(np.abs(w64))))
+    return {"problems": len(sub), "steps": "min(steps, 2000)", "gpu_bit_exact": bool(exact),
+            "max_err_ks_f32c_vs_oracle_f64": worst}
 
 
 def report_adjoint_c4(peaks, flush):

@@ -319,7 +319,8 @@ int swept_edge_copy(swept_plan_t plan, int64_t k, int window, int side, void *bu
  * (swept_adjoint_scratch returns it; N = 2^20, 20000 steps, h = 64: m = 2,
  * 349 states, 2.9 GB); none for heat.
  * Errors: SWEPT_EINVAL (null or misaligned pointers, grad_u0 == u0, memory of
- * another device), SWEPT_ENOTSUP (F32C, F32, Runge-Kutta or Euler plan),
+ * another device, KS with nsteps >= 2^31), SWEPT_ENOTSUP (F32C, F32,
+ * Runge-Kutta or Euler plan),
  * SWEPT_ENOMEM (the scratch does not fit), SWEPT_ECUDA.
  */
 int swept_adjoint(swept_plan_t plan, const void *u0, const void *lambda_T, void *grad_u0,

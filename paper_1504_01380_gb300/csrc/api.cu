@@ -783,6 +783,7 @@ int swept_adjoint(swept_plan_t p, const void* u0, const void* lam_T, void* grad,
     // same update with the same rounding: the adjoint is the forward sweep.
     return swept_advance(p, grad, nsteps, stream);
   }
+  if (nsteps > 0x7fffffff) return SWEPT_EINVAL;     // tape levels are 32-bit indices
   const AdjLayout L = adjoint_layout(p, nsteps, K_cycles);
   const size_t need = (size_t)L.states * bytes;
   if (p->adj_bytes < need) {
