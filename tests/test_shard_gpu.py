@@ -105,3 +105,59 @@ def test_stage_and_edge_copy_arguments(cuda_lib):
         with pytest.raises(sw.SweptError):
             sw.swept_edge_copy(plan, 1, w, side, buf, False)
     plan.destroy()
+
+
+def test_sharded_runge_kutta_and_euler(cuda_lib):
+    """The sharded path for the schemes with several sub-timesteps per time step and wider
+    point states: KS by the Runge-Kutta rule (levels = 2 x steps; (u, m) edge pairs) and the
+    Euler equations in compensated FP32 (levels = 4 x steps; the state's six blocks of N/G
+    floats per slice; 48-byte edge elements), three slices on this GPU against the oracle."""
+    import torch
+    from tests.test_euler_gpu import state as euler_state
+    sw = cuda_lib
+    # Runge-Kutta KS, FP64
+    B, world = 128, 3
+    N = world * 4 * B
+    prm = params_of(1)
+    u0 = workloads.ks_smoothed(N, 95) * 10.0
+    for nsteps in (3 * (B // 8) + 2, 5 * (B // 8)):       # h = B/4 levels = B/8 steps
+        box, progs, runs = {}, [], []
+        for rank in range(world):
+            sl = shard.Slice(N, B, world, rank)
+            plan = sw.swept_plan(sl.n_local, 2, sw.SWEPT_KS_RK2, prm, sw.SWEPT_F64, B)
+            u = torch.tensor(u0[sl.start:sl.start + sl.n_local], device="cuda")
+            run = shard.PlanRunner(plan, u)
+            runs.append(run)
+            progs.append(shard.ShardedAdvance(run, LoopbackTransport(rank, box), sl, plan.h, 2,
+                                              2 * nsteps).program())
+        assert shard.drive_in_process(progs, timeout_s=10) == shard.SWEPT_OK
+        torch.cuda.synchronize()
+        got = np.concatenate([r.u.cpu().numpy() for r in runs])
+        assert np.array_equal(got, oracle.advance_rk2_f64(3, prm, u0, nsteps)), nsteps
+    # Euler equations, compensated FP32
+    B, world = 64, 2
+    N = world * 5 * B
+    q, prm_e = euler_state(N, 96)                       # (N, 3) rows
+    for nsteps in (3 * (B // 8) + 1, 4 * (B // 8)):     # h = B/2 levels = B/8 steps
+        box, progs, runs = {}, [], []
+        for rank in range(world):
+            sl = shard.Slice(N, B, world, rank)
+            part = q[sl.start:sl.start + sl.n_local]
+            planar = np.concatenate([part[:, 0], part[:, 1], part[:, 2]])
+            plan = sw.swept_plan(sl.n_local, 1, sw.SWEPT_EULER, prm_e, sw.SWEPT_F32C, B)
+            u = sw.swept_f32c_split(torch.tensor(planar, device="cuda"))
+            run = shard.PlanRunner(plan, u)
+            runs.append(run)
+            progs.append(shard.ShardedAdvance(run, LoopbackTransport(rank, box), sl, plan.h, 1,
+                                              4 * nsteps).program())
+        assert shard.drive_in_process(progs, timeout_s=10) == shard.SWEPT_OK
+        torch.cuda.synchronize()
+        hi, lo = oracle.split_f32c(np.ascontiguousarray(q).reshape(-1))
+        whi, wlo = oracle.euler_advance_f32c(prm_e, hi.reshape(-1, 3), lo.reshape(-1, 3), nsteps)
+        n = N // world
+        for rank, run in enumerate(runs):
+            a = run.u.cpu().numpy()
+            ghi = a[:3 * n].reshape(3, n).T
+            glo = a[3 * n:].reshape(3, n).T
+            assert np.array_equal(ghi, whi[rank * n:(rank + 1) * n]), (nsteps, rank)
+            assert np.array_equal(glo, wlo[rank * n:(rank + 1) * n]), (nsteps, rank)
