@@ -35,8 +35,8 @@
 // Every boundary position is r*(level) plus a constant, so with levels in
 // phases of S/r the boundary stays in one lane and moves r registers per
 // level; the register offsets are compile-time, selected by a uniform branch
-// tree as in the per-window kernel (a switch for the compensated KS ring,
-// measured faster there).  The values computed are exactly those
+// tree as in the per-window kernel (a switch for the compensated KS ring up to
+// K = 16, measured faster there).  The values computed are exactly those
 // of the per-window kernel (same expression per point, only the order of
 // independent updates changes), so results are bit-identical.
 #pragma once
@@ -52,11 +52,13 @@ namespace swept {
 
 // How a level's phase step J reaches its compile-time register offsets: a
 // binary tree of uniform branches (default) or one switch.  Measured on
-// GB300: the switch is 3-12% faster for the compensated KS ring (N = 2^22,
-// B = 512 and 1024) and 9% slower for the compensated heat ring (N = 2^24);
-// FP64 KS and the compensated Euler equations differ by under 1%.
-template <int ST, class DT> struct SwitchSelect { static constexpr bool value = false; };
-template <> struct SwitchSelect<kKS, F32C> { static constexpr bool value = true; };
+// GB300: for the compensated KS ring the switch is faster at K = 16 (N = 2^22,
+// B = 512: 1.141 against 1.121e12 cell-updates/s) and the tree at K = 32
+// (B = 1024: 1.344 against 1.304e12); the switch is 9% slower for the
+// compensated heat ring (N = 2^24); FP64 KS and the compensated Euler
+// equations differ by under 1%.
+template <int ST, class DT, int K> struct SwitchSelect { static constexpr bool value = false; };
+template <int K> struct SwitchSelect<kKS, F32C, K> { static constexpr bool value = K <= 16; };
 
 template <int ST, class DT, int K>
 struct RingImpl {
@@ -149,7 +151,7 @@ struct RingImpl {
   }
   template <class F>
   static __device__ __forceinline__ void select_j(int j, F&& f) {
-    if constexpr (SwitchSelect<ST, DT>::value) select_switch(j, f);
+    if constexpr (SwitchSelect<ST, DT, K>::value) select_switch(j, f);
     else select<0, L>(j, f);
   }
 
