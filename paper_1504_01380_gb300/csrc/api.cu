@@ -96,6 +96,12 @@ int make_consts(int stencil, const double* p, int np, Consts& c) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+int sm_count(const swept_plan_s* p) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  return sms;
+}
+
 cudaError_t launch_stage(const swept_plan_s* p, const StageArgs& a, cudaStream_t s) {
   if (p->stencil == SWEPT_EULER)
     return p->dtype == SWEPT_F64 ? swept::launch_stage_euler_f64(p->K, a, s)
@@ -497,24 +503,36 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s, co
     ++nlaunch;
     if (full) ++nring;
     if (!uneven) return full ? launch_ring(p, a, s) : launch_stage(p, a, s);
-    // uneven tiles: the B-wide windows (ring or per window), then the wide ones
+    // uneven tiles: the B-wide windows (ring or per window) and the wide ones;
+    // a full diamond stage on the ring runs both in one launch (except for the
+    // Euler equations, whose ring would lose a block per SM to the wide
+    // windows' larger shared memory)
+    const int odd = (int)(k & 1);
+    const int w = (p->diamond == SWEPT_DIAMOND_AUTO && p->ring_warps == 0) ? -1 : p->ring_warps;
+    const bool joint = full && p->stencil != SWEPT_EULER &&
+                       (w >= 0 || (int64_t)p->nreg > 4 * (int64_t)sm_count(p));
     cudaError_t e = cudaSuccess;
-    if (p->nreg > 0) {
+    if (p->nreg > 0 && !joint) {
       a.nlaunch = p->nreg;
       e = full ? launch_ring(p, a, s) : launch_stage(p, a, s);
       a.nlaunch = 0;
       ++nlaunch;
     }
     if (e != cudaSuccess) return e;
-    const int odd = (int)(k & 1);
-    if (p->stencil == SWEPT_EULER) return swept::launch_wide_euler(p->dtype, p->K, a, p->nreg, odd, s);
-    if (p->stencil == SWEPT_HEAT_RK2)
-      return swept::launch_wide_rk2(swept::kHeatRK2, p->K, a, p->nreg, odd, s);
-    if (p->stencil == SWEPT_KS_RK2) return swept::launch_wide_rk2(swept::kKSRK2, p->K, a, p->nreg, odd, s);
-    const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
-    if (p->dtype == SWEPT_F64) return swept::launch_wide_f64(st, p->K, a, p->nreg, odd, s);
-    if (p->dtype == SWEPT_F32C) return swept::launch_wide_f32c(st, p->K, a, p->nreg, odd, s);
-    return swept::launch_wide_f32(st, p->K, a, p->nreg, odd, s);
+    const int ring = joint ? (w > 0 ? w : 0) : -1;
+    a.nlaunch = joint ? p->nreg : 0;
+    if (p->stencil == SWEPT_EULER) e = swept::launch_wide_euler(p->dtype, p->K, a, p->nreg, odd, s);
+    else if (p->stencil == SWEPT_HEAT_RK2)
+      e = swept::launch_wide_rk2(swept::kHeatRK2, p->K, a, p->nreg, odd, s, ring);
+    else if (p->stencil == SWEPT_KS_RK2) e = swept::launch_wide_rk2(swept::kKSRK2, p->K, a, p->nreg, odd, s, ring);
+    else {
+      const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
+      if (p->dtype == SWEPT_F64) e = swept::launch_wide_f64(st, p->K, a, p->nreg, odd, s, ring);
+      else if (p->dtype == SWEPT_F32C) e = swept::launch_wide_f32c(st, p->K, a, p->nreg, odd, s, ring);
+      else e = swept::launch_wide_f32(st, p->K, a, p->nreg, odd, s, ring);
+    }
+    a.nlaunch = 0;
+    return e;
   };
   cudaError_t e = cudaSuccess;
   if (q == 0) {

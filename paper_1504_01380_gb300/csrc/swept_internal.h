@@ -200,11 +200,14 @@ cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double
 // B + 32r wide.  One warp per wide window does its V (a regular B window
 // centred on the previous stage's boundary, stored flat to u) and then its
 // trapezoid of the full width from u.  K in {1, 2, 4, 8, 16} (multiple of r;
-// Euler equations: K <= 4 in FP64, K <= 8 compensated).
-cudaError_t launch_wide_f64(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
-cudaError_t launch_wide_f32c(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
-cudaError_t launch_wide_f32(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
-cudaError_t launch_wide_rk2(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
+// Euler equations: K <= 4 in FP64, K <= 8 compensated).  ring < 0 launches
+// the wide windows alone; ring >= 0 a full diamond stage in one launch, the
+// ring over the a.nlaunch = nreg regular windows with `ring` warps (0:
+// automatic) beside one warp per wide window.
+cudaError_t launch_wide_f64(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s, int ring);
+cudaError_t launch_wide_f32c(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s, int ring);
+cudaError_t launch_wide_f32(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s, int ring);
+cudaError_t launch_wide_rk2(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s, int ring);
 cudaError_t launch_wide_euler(int dtype, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 // The transposed KS step (adjoint sweeps) on the wide windows, FP64, K in {2, 4, 8, 16}.
 cudaError_t launch_wide_ksadj(int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);

@@ -190,8 +190,9 @@ def test_ks_adjoint_full_size_fd_converges(cuda_lib):
     """N = 2^20, 20000 steps, checkpoints every 64 cycles (the adjoint workload).
 
     Over 40 time units the chaotic dynamics amplify the O(eps^2) truncation of the
-    central difference, so agreement is checked by convergence: halving eps must
-    shrink |FD - AD| about fourfold (quadratic), i.e. FD tends to the adjoint.
+    central difference D(eps): halving eps must shrink |D - AD| about fourfold
+    (quadratic), and the Richardson combination (4 D(eps/2) - D(eps)) / 3, which
+    cancels the eps^2 term, must agree with the adjoint within 1e-6.
     """
     sw = cuda_lib
     n, nsteps = 1 << 20, 20000
@@ -203,10 +204,13 @@ def test_ks_adjoint_full_size_fd_converges(cuda_lib):
     for d in range(4):
         v = workloads.fd_direction(n, d)
         ad = math.fsum(g * v)
-        errs = []
+        errs, fds = [], []
         for eps in (1e-6, 5e-7, 2.5e-7):
             fd = (J(u0 + eps * v)[0] - J(u0 - eps * v)[0]) / (2 * eps)
+            fds.append(fd)
             errs.append(abs(fd - ad) / abs(ad))
+        rich = (4 * fds[2] - fds[1]) / 3
+        assert abs(rich - ad) <= 1e-6 * abs(ad), (d, rich, ad, errs)
         assert errs[0] <= 1e-2, (d, errs)
         if errs[0] > 1e-4:           # truncation-dominated: must converge quadratically
             assert errs[1] <= errs[0] / 2.5 and errs[2] <= errs[1] / 2.5, (d, errs)

@@ -125,3 +125,46 @@ def test_uneven_adjoint_matches_oracle(cuda_lib, N, B, ring):
                                nsteps, K).cpu().numpy()
         want = oracle.adjoint_f64(KS, params_of(KS), u0, lam, nsteps)
         assert np.array_equal(got, want), (N, B, nsteps, K, np.flatnonzero(got != want)[:8])
+
+
+# A full diamond stage of an uneven tiling on the ring runs the ring over the regular windows and
+# the wide windows in one launch (one warp per wide window beside the ring's runs): forced at small
+# N (the ring kernel with a few warps, or with its automatic warp count), automatic where the
+# regular windows outnumber four per SM.  (stencil, dtype, B, N, ring warps: None = automatic
+# choice of kernel, 0 = ring with automatic warps)
+JOINT = [(HEAT, F64, 128, 128 * 25 + 100, 3), (HEAT, F32C, 128, 128 * 12 + 33, 0), (HEAT, F32, 64, 64 * 15 + 7, 2),
+         (KS, F64, 128, 128 * 20 + 100, 4), (KS, F32C, 512, 512 * 12 + 300, 3), (KS, F32, 256, 256 * 10 + 130, 0),
+         (HEAT, F32C, 32, 32 * 700 + 7, None), (KS, F32C, 64, 64 * 700 + 50, None)]
+
+
+@pytest.mark.parametrize("stencil,dtype,B,N,warps", JOINT)
+def test_uneven_joint_ring_and_wide_launch(cuda_lib, stencil, dtype, B, N, warps):
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, B)
+    if warps is not None:
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, warps)
+    h = plan.h
+    u0 = initial(stencil, N, 9700 + N)
+    for nsteps in (h + 1, 4 * h, 5 * h + h // 2 + 1):
+        assert_same(plan, run_gpu(sw, plan, u0, nsteps), oracle_run(stencil, dtype, u0, nsteps))
+    # 5h + h/2 + 1 steps: the triangle, 4 diamonds (one launch each), the last V-fill with the
+    # remainder's trapezoid, and the remainder's V-fill (two launches for each of those three)
+    assert sw.swept_plan_last_advance(plan)[:2] == (4 + 3 * 2, 4)
+
+
+def test_uneven_joint_launch_runge_kutta(cuda_lib):
+    """The joint launch for the Runge-Kutta pairs (forced ring, two and three warps)."""
+    import oracle
+    from tests.test_rk2_gpu import prm, initial as rk2_initial, run as rk2_run
+    sw = cuda_lib
+    for st, B, N, warps in ((2, 64, 64 * 30 + 20, 2), (3, 128, 128 * 20 + 70, 3)):
+        r = 1 if st == 2 else 2
+        plan = sw.swept_plan(N, r, st, prm(st), F64, B)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, warps)
+        per = plan.h // 2
+        u0 = rk2_initial(st, N, 9800 + N)
+        for nsteps in (per + 1, 4 * per + 3):
+            assert np.array_equal(rk2_run(sw, plan, u0, nsteps), oracle.advance_rk2_f64(st, prm(st), u0, nsteps))
