@@ -614,9 +614,12 @@ def report_heat_f64(peaks, flush):
 
 
 def report_latency_c0(peaks, flush):
-    """Heat, N = 1024, r = 1/4, 2000 steps, FP64, B = 32: the latency regime.  Per
-    sub-timestep, the swept stages (graph-replayed) against the naive stepper (graph-replayed),
-    the fit of Eq. 1 over B, and the compensated FP32 state."""
+    """Heat, N = 1024, r = 1/4, 2000 steps, FP64, B = 32: the latency regime.  Per sub-timestep:
+    the swept advance in one thread block cluster (the stage edges in shared memory, a cluster
+    barrier between stages: the default where the problem fits one cluster) and with one launch
+    per stage (graph-replayed), against the naive stepper with its steps in one cluster (one
+    cluster barrier per step) and with one launch per step (graph-replayed); Eq. 1 fitted over
+    B for both kinds of stage boundary; the compensated FP32 state."""
     import torch
     import paper_1504_01380_gb300 as sw
     from paper_1504_01380_gb300 import tune
@@ -625,83 +628,91 @@ def report_latency_c0(peaks, flush):
     u0_dev = torch.tensor(u0, device="cuda")
     u = u0_dev.clone()
 
-    def per_sub(fn, reps=5):
+    def per_sub(fn, x, x0, reps=5):
         fn()
         torch.cuda.synchronize()
         best = float("inf")
         for _ in range(reps):
-            u.copy_(u0_dev)
+            x.copy_(x0)
             best = min(best, cuda_time(fn))
         return best / nsteps
 
-    graph = {}
-    for B in (32, 64, 128, 256):
-        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, B)
-        sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
-        graph[B] = per_sub(lambda: sw.swept_advance(plan, u, nsteps))
-        if B == 32:
-            u.copy_(u0_dev)
-            sw.swept_advance(plan, u, nsteps)
-            got32 = u.cpu().numpy()
-            launches = sw.swept_plan_last_advance(plan)[0]
-            h32 = plan.h
+    def swept_times(dtype, x, x0, widths):
+        res, launch = {}, {}
+        for B in widths:
+            plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], dtype, B)
+            t = per_sub(lambda: sw.swept_advance(plan, x, nsteps), x, x0)
+            if sw.swept_plan_last_advance(plan)[0] == 1:        # one cluster launch (K <= 4)
+                res[B] = t
+            sw.swept_plan_set(plan, sw.SWEPT_OPT_RESIDENT, 0)
+            sw.swept_plan_set(plan, sw.SWEPT_OPT_GRAPH, 1)
+            launch[B] = per_sub(lambda: sw.swept_advance(plan, x, nsteps), x, x0)
+            plan.destroy()
+        return res, launch
+
+    def naive_times(dtype, x, x0):
+        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], dtype, 32)
+        g = torch.cuda.CUDAGraph()
+        x.copy_(x0)
+        with torch.cuda.graph(g):
+            sw.swept_naive_advance(plan, x, nsteps)
+        t_graph = per_sub(g.replay, x, x0, reps=3)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_NAIVE_RESIDENT, 1)
+        t_res = per_sub(lambda: sw.swept_naive_advance(plan, x, nsteps), x, x0)
         plan.destroy()
-    plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, 32)
-    g = torch.cuda.CUDAGraph()
-    u.copy_(u0_dev)
-    with torch.cuda.graph(g):
-        sw.swept_naive_advance(plan, u, nsteps)
-    naive = per_sub(g.replay, reps=3)
-    plan.destroy()
+        return t_graph, t_res
+
+    widths = (32, 64, 128, 256)
+    res, launch = swept_times(sw.SWEPT_F64, u, u0_dev, widths)
+    naive, naive_res = naive_times(sw.SWEPT_F64, u, u0_dev)
+    # the result of each path at B = 32
+    got = {}
+    for resident in (1, 0):
+        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F64, 32)
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_RESIDENT, resident)
+        u.copy_(u0_dev)
+        sw.swept_advance(plan, u, nsteps)
+        got[resident] = u.cpu().numpy()
+        if resident == 0:
+            launches, h32 = sw.swept_plan_last_advance(plan)[0], plan.h
+        plan.destroy()
     # compensated FP32 state
     c0 = sw.swept_f32c_split(u0_dev)
     c = c0.clone()
-
-    def per_sub32(fn, reps=5):
-        fn()
-        torch.cuda.synchronize()
-        best = float("inf")
-        for _ in range(reps):
-            c.copy_(c0)
-            best = min(best, cuda_time(fn))
-        return best / nsteps
-
-    f32c = {}
-    for B in (32, 64):
-        p = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, B)
-        sw.swept_plan_set(p, sw.SWEPT_OPT_GRAPH, 1)
-        f32c[B] = per_sub32(lambda: sw.swept_advance(p, c, nsteps))
-        p.destroy()
-    p = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, 32)
-    g3 = torch.cuda.CUDAGraph()
-    c.copy_(c0)
-    with torch.cuda.graph(g3):
-        sw.swept_naive_advance(p, c, nsteps)
-    naive32 = per_sub32(g3.replay, reps=3)
-    p.destroy()
-    fit = tune.fit_eq1([(B, t) for B, t in graph.items()])
+    res32, launch32 = swept_times(sw.SWEPT_F32C, c, c0, (32, 64))
+    naive32, naive32_res = naive_times(sw.SWEPT_F32C, c, c0)
+    fit = tune.fit_eq1([(B, t) for B, t in launch.items()])
+    fit_res = tune.fit_eq1([(B, t) for B, t in res.items()])
     exact = exact_heat(u0, HEAT_R, nsteps)
-    err = float(np.max(np.abs(got32 - exact)) / np.max(np.abs(u0)))
-    oracle_leg = cpu_leg_latency(u0, nsteps, got32)
-    t32 = graph[32]
-    best32 = min(f32c, key=f32c.get)
-    # the launch gap: the naive graph's time per sub-timestep is one kernel boundary plus
-    # 1024 points of work; a stage of h sub-timesteps pays it once
+    err = float(np.max(np.abs(got[1] - exact)) / np.max(np.abs(u0)))
+    oracle_leg = cpu_leg_latency(u0, nsteps, got[1])
+    oracle_leg["stage_launches_equal_resident"] = bool(np.array_equal(got[0], got[1]))
+    t32, tl32 = res[32], launch[32]
+    ns = lambda d: {str(B): t * 1e9 for B, t in d.items()}
+    eq1 = lambda f: {"s_ns": f["s"] * 1e9, "tau_ns": f["tau"] * 1e9, "n_star": f["n_star"]} if f else None
     return {"workload": "heat1d_N1024_r0.25_2000steps_f64_B32", "unit": "ns per sub-timestep",
-            "swept_graph_ns": t32 * 1e9, "naive_graph_ns": naive * 1e9, "speedup_vs_naive_graph": naive / t32,
-            "swept_graph_ns_by_B": {str(B): t * 1e9 for B, t in graph.items()},
-            "launches": launches,
+            "swept_ns": t32 * 1e9, "swept_path": "one thread block cluster (stage edges in shared memory, cluster barriers)",
+            "swept_ns_by_B": ns(res),
+            "swept_stage_launches_graph_ns": tl32 * 1e9, "swept_stage_launches_graph_ns_by_B": ns(launch),
+            "stage_launches": launches,
+            "naive_resident_ns": naive_res * 1e9, "naive_graph_ns": naive * 1e9,
+            "speedup_vs_naive_resident": naive_res / t32, "speedup_vs_naive_graph": naive / t32,
+            "stage_launches_speedup_vs_naive_graph": naive / tl32,
             "max_err_vs_closed_form": err,
             "error_reference": "closed form sum_k g_k^n (a_k sin + b_k cos), relative to max|u0|",
-            "f32c": {"swept_graph_ns_by_B": {str(B): t * 1e9 for B, t in f32c.items()},
-                     "naive_graph_ns": naive32 * 1e9, "speedup_vs_naive_graph": naive32 / f32c[best32]},
-            "eq1_fit": {"s_ns": fit["s"] * 1e9, "tau_ns": fit["tau"] * 1e9, "n_star": fit["n_star"]} if fit else None,
-            "roofline": {"bound": "latency", "achieved": t32 * 1e9, "unit": "ns per sub-timestep",
-                         "peak": naive * 1e9 / h32, "frac": (naive / h32) / t32,
+            "f32c": {"swept_ns_by_B": ns(res32), "swept_stage_launches_graph_ns_by_B": ns(launch32),
+                     "naive_resident_ns": naive32_res * 1e9, "naive_graph_ns": naive32 * 1e9,
+                     "speedup_vs_naive_resident": naive32_res / min(res32.values()),
+                     "speedup_vs_naive_graph": naive32 / min(res32.values())},
+            "eq1_fit_stage_launches": eq1(fit), "eq1_fit_resident": eq1(fit_res),
+            "roofline": {"bound": "latency", "achieved": tl32 * 1e9, "unit": "ns per sub-timestep",
+                         "peak": naive * 1e9 / h32, "frac": (naive / h32) / tl32,
+                         "kernel": "per-stage launches (graph-replayed)",
                          "peak_source": ("measured: one kernel boundary (the graph-replayed naive stepper's "
                                          "time per sub-timestep) paid once per stage of h = 16 sub-timesteps; "
                                          "the rest of the time is the per-level dependence chain of one warp")},
             "cpu_baseline": oracle_leg}
+
 
 
 def cpu_leg_latency(u0, nsteps, got):

@@ -188,6 +188,27 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        read by swept_plan_last_advance.  0 (default): none.
  *   SWEPT_OPT_TIMEOUT_MS budget of each persistent or streamed wait,
  *                        1..600000 ms (2000).
+ *   SWEPT_OPT_RESIDENT   1 (default): an advance of an evenly tiled heat or KS
+ *                        plan (forward Euler with K <= 4, Runge-Kutta pairs
+ *                        with K <= 2) of at most 64 windows, with the automatic
+ *                        kernel choice (SWEPT_DIAMOND_AUTO, automatic warps) and
+ *                        neither SWEPT_OPT_PERSISTENT nor SWEPT_OPT_DROP_WINDOW,
+ *                        runs in one launch of one thread block cluster (at most
+ *                        16 blocks of 4, 2 or 1 warps, one warp per window) when
+ *                        the GPU can hold it: each block keeps its windows' stage
+ *                        edges in shared memory, the V-fills read their
+ *                        neighbours' edges through distributed shared memory,
+ *                        and a cluster barrier separates the stages (the latency
+ *                        regime of Section 4, without a kernel launch or a
+ *                        global-memory round trip per stage).  0: the per-stage
+ *                        launches.
+ *   SWEPT_OPT_NAIVE_RESIDENT 1: swept_naive_advance of a forward-Euler heat or
+ *                        KS plan runs every step in one thread block cluster
+ *                        when N splits into at most 16 parts of 4r to 4094
+ *                        points (each block steps its part in shared memory
+ *                        with r halo points from its neighbours, one cluster
+ *                        barrier per step: the per-step counterpart of
+ *                        SWEPT_OPT_RESIDENT); 0 (default): one launch per step.
  *   SWEPT_OPT_DROP_WINDOW failure injection: in the persistent advance window
  *                        `value`, in a streamed ring launch warp `value`, never
  *                        publishes its progress (a lost message), so the waits
@@ -203,6 +224,8 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
 #define SWEPT_OPT_TIMEOUT_MS  6
 #define SWEPT_OPT_STREAM      7
 #define SWEPT_OPT_TIME_RING   8
+#define SWEPT_OPT_RESIDENT    9
+#define SWEPT_OPT_NAIVE_RESIDENT 10
 #define SWEPT_DIAMOND_AUTO    0
 #define SWEPT_DIAMOND_WINDOW  1
 #define SWEPT_DIAMOND_RING    2

@@ -23,6 +23,7 @@ SWEPT_ETOOBIG = -6
 SWEPT_NOALLOC_MAX_N = 1 << 20
 SWEPT_OPT_DIAMOND, SWEPT_OPT_RING_WARPS, SWEPT_OPT_GRAPH, SWEPT_OPT_PDL, SWEPT_OPT_PERSISTENT = 0, 1, 2, 3, 4
 SWEPT_OPT_DROP_WINDOW, SWEPT_OPT_TIMEOUT_MS, SWEPT_OPT_STREAM, SWEPT_OPT_TIME_RING = 5, 6, 7, 8
+SWEPT_OPT_RESIDENT, SWEPT_OPT_NAIVE_RESIDENT = 9, 10
 SWEPT_DIAMOND_AUTO, SWEPT_DIAMOND_WINDOW, SWEPT_DIAMOND_RING = 0, 1, 2
 SWEPT_PROBE_F32_ADD, SWEPT_PROBE_F32_FMA, SWEPT_PROBE_F64_ADD, SWEPT_PROBE_F64_FMA = 0, 1, 2, 3
 

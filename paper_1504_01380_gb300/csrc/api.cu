@@ -41,6 +41,8 @@ struct swept_plan_s {
   double timeout_s;       // SWEPT_OPT_TIMEOUT_MS / 1000: budget of each persistent or streamed wait
   int stream;             // SWEPT_OPT_STREAM: ring stages of an advance in one launch
   int time_ring;          // SWEPT_OPT_TIME_RING: events around the ring launches of each advance
+  int resident;           // SWEPT_OPT_RESIDENT: block-resident advance where the problem fits one block
+  int naive_resident;     // SWEPT_OPT_NAIVE_RESIDENT: the naive stepper's steps in one block
   cudaEvent_t ring_ev[2];
   int ring_timed;         // the last advance recorded ring_ev
   int64_t last_launches, last_ring_launches;
@@ -243,6 +245,7 @@ int swept_plan(swept_plan_t* out, int64_t N, int radius, int stencil_id, const d
   p->drop_w = -1;
   p->timeout_s = 2.0;
   p->stream = 1;
+  p->resident = 1;
   cudaGetDevice(&p->device);
   const size_t esize = euler ? (dtype == SWEPT_F64 ? sizeof(swept::EulerE) : sizeof(swept::EulerEF))
                               : (rk2 ? 16 : (dtype == SWEPT_F32 ? 4 : 8));
@@ -304,6 +307,15 @@ int swept_plan_set(swept_plan_t p, int option, int64_t value) {
     if (value != 0 && value != 1) return SWEPT_EINVAL;
     p->use_graph = (int)value;
     if (p->g_valid) {              // the captured launches carry the old setting
+      cudaGraphExecDestroy(p->gexec);
+      p->g_valid = 0;
+    }
+    return SWEPT_OK;
+  }
+  if (option == SWEPT_OPT_RESIDENT || option == SWEPT_OPT_NAIVE_RESIDENT) {
+    if (value != 0 && value != 1) return SWEPT_EINVAL;
+    (option == SWEPT_OPT_RESIDENT ? p->resident : p->naive_resident) = (int)value;
+    if (p->g_valid) {
       cudaGraphExecDestroy(p->gexec);
       p->g_valid = 0;
     }
@@ -397,6 +409,36 @@ bool persistent_ok(const swept_plan_s* p, int64_t levels) {
   return fits != 0;
 }
 
+// Internal stencil id of a plan.
+int internal_stencil(const swept_plan_s* p) {
+  switch (p->stencil) {
+    case SWEPT_HEAT: return swept::kHeat;
+    case SWEPT_KS: return swept::kKS;
+    case SWEPT_HEAT_RK2: return swept::kHeatRK2;
+    case SWEPT_KS_RK2: return swept::kKSRK2;
+    default: return swept::kEuler;
+  }
+}
+
+// The cluster-resident advance (SWEPT_OPT_RESIDENT) applies to evenly tiled
+// heat and KS plans (forward Euler, K <= 4; Runge-Kutta pairs, K <= 2) of at
+// most 64 windows whose cluster fits the GPU, with the automatic kernel
+// choice and neither the persistent advance nor failure injection asked for.
+bool resident_ok(const swept_plan_s* p, int64_t levels) {
+  if (!p->resident || p->persistent || p->drop_w >= 0 || p->nreg != p->nwin || p->nwin > 64) return false;
+  if (p->diamond != SWEPT_DIAMOND_AUTO || p->ring_warps != 0) return false;
+  if (p->stencil == SWEPT_EULER || p->K > (p->rk2 ? 2 : 4)) return false;
+  if (levels / p->H > (int64_t)0x3fffffff) return false;
+  swept::ResidentArgs ra{};
+  ra.a.nwin = p->nwin;
+  int fits = 0;
+  if (swept::launch_resident(internal_stencil(p), p->dtype, p->K, ra, nullptr, false, true, &fits) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return fits != 0;
+}
+
 // Clock cycles of one bounded wait (SWEPT_OPT_TIMEOUT_MS at the SM clock).
 long long wait_budget(const swept_plan_s* p) {
   int dev = 0, khz = 0;
@@ -443,6 +485,21 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s, co
   const int64_t H = p->H;
   const int64_t q = levels / H;
   const int rem = (int)(levels % H);
+  if (!dumps && levels > 0 && resident_ok(p, levels)) {
+    swept::ResidentArgs ra{};
+    ra.a.u = u;
+    ra.a.N = p->N;
+    ra.a.nwin = p->nwin;
+    ra.a.c = p->c;
+    ra.q = (int)q;
+    ra.rem = rem;
+    ra.H = (int)H;
+    ra.nstages = q == 0 ? 2 : (rem ? (int)q + 2 : (int)q + 1);
+    p->last_launches = 1;
+    p->last_ring_launches = 0;
+    p->ring_timed = 0;
+    return cuda_status(swept::launch_resident(internal_stencil(p), p->dtype, p->K, ra, s, p->pdl != 0, false, nullptr));
+  }
   if (!dumps && persistent_ok(p, levels)) {
     swept::PersistArgs pa{};
     pa.a.u = u;
@@ -879,6 +936,14 @@ int swept_naive_advance(swept_plan_t p, void* u, int64_t nsteps, void* stream) {
     if (e == cudaSuccess && cur == 1)
       e = cudaMemcpyAsync(u, bufs[1], (size_t)p->N * 8, cudaMemcpyDeviceToDevice, s);
     return cuda_status(e);
+  }
+  if (p->naive_resident && nsteps > 0) {
+    const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
+    int fits = 0;
+    cudaError_t e = swept::launch_naive_resident(st, p->dtype, u, p->N, p->c, nsteps, s, false, true, &fits);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (fits) return cuda_status(swept::launch_naive_resident(st, p->dtype, u, p->N, p->c, nsteps, s, p->pdl != 0,
+                                                               false, nullptr));
   }
   void* bufs[2] = {u, p->edges};
   cudaError_t e = cudaSuccess;

@@ -10,7 +10,12 @@
 // which the neighbouring warp's loads have usually brought into L2 already.
 // When N is not a multiple of V the last thread owns the N mod V points left,
 // loaded and stored one by one, and its right neighbours wrap to the start.
+#include <cooperative_groups.h>
+#include <type_traits>
+
 #include "swept_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace swept {
 
@@ -30,14 +35,14 @@ template <> __device__ __forceinline__ float hi_at<F32>(const void* u, int64_t g
   return static_cast<const float*>(u)[g];
 }
 
+// One sub-timestep of the kV points of the thread starting at i0 (in, out:
+// whole fields, in global or shared memory).  Every lane of the warp calls
+// it (the shuffles); lanes past the field's end store nothing.
 template <int ST, class DT>
-__global__ void __launch_bounds__(kNaiveThreads)
-naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N, const Consts c) {
+__device__ __forceinline__ void naive_points(const void* __restrict__ in, void* __restrict__ out, int64_t N,
+                                             const Consts& c, int64_t i0, int lane) {
   constexpr int R = Radius<ST>::value;
-  griddep_wait();
   using Cc = typename DT::C;
-  const int lane = threadIdx.x & 31;
-  const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
   const bool valid = i0 < N;
   // the last thread of a field whose N is not a multiple of V owns fewer points
   const int64_t left = N - i0;
@@ -101,6 +106,62 @@ naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N
     for (int k = 0; k < kV; ++k)
       if (k < left) store_point<kV>(t, k, out, N, i0 + k);
   }
+}
+
+template <int ST, class DT>
+__global__ void __launch_bounds__(kNaiveThreads)
+naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N, const Consts c) {
+  griddep_wait();
+  const int64_t i0 = ((int64_t)blockIdx.x * kNaiveThreads + threadIdx.x) * kV;
+  naive_points<ST, DT>(in, out, N, c, i0, threadIdx.x & 31);
+}
+
+// Every step of a naive advance in one thread block cluster (the per-step
+// counterpart of the cluster-resident swept advance): the field is split over
+// the C blocks, M = N / C points each, held in shared memory with R halo
+// points per side, [R halo | M own | R halo], in two buffers (hi then lo for
+// a compensated field).  Each step refreshes the halos from the neighbouring
+// blocks' own points through distributed shared memory, steps the padded
+// field (its own points need no wrap) into the other buffer, and ends with a
+// cluster barrier: one barrier per sub-timestep where the swept advance
+// needs one per stage.
+template <int ST, class DT>
+__global__ void __launch_bounds__(1024, 1)
+naive_cluster_kernel(void* __restrict__ u, int64_t N, const Consts c, int64_t nsteps, int M) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int R = Radius<ST>::value;
+  constexpr int NC = std::is_same<DT, F32C>::value ? 2 : 1;   // components (hi, lo)
+  using Cc = typename DT::C;
+  cg::cluster_group cl = cg::this_cluster();
+  griddep_wait();
+  const int L = M + 2 * R;                                   // padded field
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int left = (rank + C - 1) % C, right = (rank + 1) % C;
+  Cc* buf[2] = {reinterpret_cast<Cc*>(smem_raw), reinterpret_cast<Cc*>(smem_raw) + NC * L};
+  const int64_t g0 = (int64_t)rank * M;
+  Cc* uc = static_cast<Cc*>(u);
+  for (int i = threadIdx.x; i < M; i += blockDim.x)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) buf[0][j * L + R + i] = uc[j * N + g0 + i];
+  cl.sync();                                                 // every block started and loaded
+  const int64_t i0 = (int64_t)threadIdx.x * kV;
+  for (int64_t k = 0; k < nsteps; ++k) {
+    Cc* cur = buf[k & 1];
+    if (threadIdx.x < 2 * R * NC) {
+      // halo point q of component j: the left block's own points M - R + q (its
+      // cur[M + q]), the right block's own points q (its cur[R + q])
+      const int j = threadIdx.x / (2 * R), q = threadIdx.x % (2 * R);
+      if (q < R) cur[j * L + q] = *cl.map_shared_rank(cur + j * L + M + q, (unsigned)left);
+      else cur[j * L + M + q] = *cl.map_shared_rank(cur + j * L + q, (unsigned)right);
+    }
+    __syncthreads();
+    naive_points<ST, DT>(cur, buf[(k + 1) & 1], L, c, i0, threadIdx.x & 31);
+    cl.sync();                                               // this step's points, read as halos next
+  }
+  const Cc* fin = buf[nsteps & 1];
+  for (int i = threadIdx.x; i < M; i += blockDim.x)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) uc[j * N + g0 + i] = fin[j * L + R + i];
 }
 
 template <int ST, class DT>
@@ -287,6 +348,57 @@ cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double
                          m, out, N, c);
   return launch_kernel(pdl, naive_rk2_kernel<kKSRK2>, dim3((unsigned)grid), dim3(kNaiveThreads), 0, s, sub, u, m,
                        out, N, c);
+}
+
+namespace {
+// Blocks C of a naive cluster: the most (at most 16) that divide N into parts
+// of at least 4R points whose padded part (M + 2R points, 4 per thread) fits
+// one block of 1024 threads.
+int naive_cluster_blocks(int64_t N, int R) {
+  for (int C = 16; C >= 1; --C) {
+    if (N % C) continue;
+    const int64_t M = N / C;
+    if (M >= 4 * R && (M + 2 * R + kV - 1) / kV <= 1024) return C;
+  }
+  return 0;
+}
+
+template <int ST, class DT>
+cudaError_t launch_res(void* u, int64_t N, const Consts& c, int64_t nsteps, cudaStream_t s, bool pdl, bool query,
+                       int* fits) {
+  constexpr int R = Radius<ST>::value;
+  constexpr int NC = std::is_same<DT, F32C>::value ? 2 : 1;
+  if (query) *fits = 0;
+  const int C = naive_cluster_blocks(N, R);
+  if (C == 0) return query ? cudaSuccess : cudaErrorInvalidValue;
+  const int M = (int)(N / C), L = M + 2 * R;
+  const size_t smem = (size_t)2 * NC * L * sizeof(typename DT::C);
+  const int threads = ((L + kV - 1) / kV + 31) / 32 * 32;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)optin) return query ? cudaSuccess : cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(naive_cluster_kernel<ST, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess && C > 8)
+    e = cudaFuncSetAttribute(naive_cluster_kernel<ST, DT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  return launch_cluster(pdl, naive_cluster_kernel<ST, DT>, dim3(C), dim3(threads), smem, s, query, fits, u, N, c,
+                        nsteps, M);
+}
+}  // namespace
+
+cudaError_t launch_naive_resident(int stencil, int dtype, void* u, int64_t N, const Consts& c, int64_t nsteps,
+                                  cudaStream_t s, bool pdl, bool query, int* fits) {
+  if (N <= 0) return cudaErrorInvalidValue;
+  if (stencil == kHeat) {
+    if (dtype == 2) return launch_res<kHeat, F32>(u, N, c, nsteps, s, pdl, query, fits);
+    return dtype == 0 ? launch_res<kHeat, F64>(u, N, c, nsteps, s, pdl, query, fits)
+                      : launch_res<kHeat, F32C>(u, N, c, nsteps, s, pdl, query, fits);
+  }
+  if (dtype == 2) return launch_res<kKS, F32>(u, N, c, nsteps, s, pdl, query, fits);
+  return dtype == 0 ? launch_res<kKS, F64>(u, N, c, nsteps, s, pdl, query, fits)
+                    : launch_res<kKS, F32C>(u, N, c, nsteps, s, pdl, query, fits);
 }
 
 cudaError_t launch_naive_step(int stencil, int dtype, const void* in, void* out, int64_t N,

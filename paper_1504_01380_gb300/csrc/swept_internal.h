@@ -150,6 +150,36 @@ inline cudaError_t launch_kernel(bool pdl, void (*kern)(KArgs...), dim3 grid, di
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// A launch of `grid` blocks as one thread block cluster (grid.x blocks,
+// at most 16; above 8 the kernel must allow non-portable cluster sizes), with
+// programmatic dependent launch when pdl.  query = true: *fits = 1 when one
+// such cluster can be resident (nothing is launched).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_cluster(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t s, bool query, int* fits, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = grid.x;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 2 : 1;
+  if (query) {
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    *fits = (e == cudaSuccess && n >= 1) ? 1 : 0;
+    return e;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Launchers, one per (stencil, dtype); K = B / 32.
 cudaError_t launch_stage_heat_f64(int K, const StageArgs& a, cudaStream_t s);
 cudaError_t launch_stage_heat_f32c(int K, const StageArgs& a, cudaStream_t s);
@@ -224,6 +254,25 @@ struct PersistArgs {
   int q, rem, H, nstages;
   int drop_w;                   // window whose publishes are dropped (a lost message; -1: none)
 };
+// Cluster-resident swept advance: the whole advance in one launch of one
+// thread block cluster (at most 16 blocks of 1, 2 or 4 warps, one warp per
+// window: nwin <= 64; K <= 4, Runge-Kutta pairs K <= 2), the stage edges in
+// the blocks' shared memory (read by the neighbours through distributed shared
+// memory), a cluster barrier between stages.
+struct ResidentArgs {
+  StageArgs a;                  // u, N, nwin, c (the per-stage fields are set on the device)
+  int q, rem, H, nstages;
+};
+// query = true: *fits = 1 when the plan's cluster can be resident.
+cudaError_t launch_resident(int stencil, int dtype, int K, const ResidentArgs& p, cudaStream_t s, bool pdl,
+                            bool query, int* fits);
+// Naive advance of nsteps sub-timesteps in one thread block cluster
+// (forward-Euler heat and KS): the field split over the blocks' shared memory,
+// each block stepping its part with R halo points from its neighbours, one
+// cluster barrier per sub-timestep; query as above.
+cudaError_t launch_naive_resident(int stencil, int dtype, void* u, int64_t N, const Consts& c, int64_t nsteps,
+                                  cudaStream_t s, bool pdl, bool query, int* fits);
+
 // query = true: *fits = 1 when every block of the launch can be resident at once.
 cudaError_t launch_persistent(int stencil, int dtype, int K, const PersistArgs& p, cudaStream_t s, bool pdl,
                               bool query, int* fits);
