@@ -149,7 +149,7 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        streams a run of windows, overlapping the V-fill of
  *                        one with the triangle of the previous).
  *   SWEPT_OPT_RING_WARPS warps of a ring launch; 0 = min(resident warp slots,
- *                        N/B/2), and at most 4 per SM for FP64 states.  A
+ *                        N/B/2), and at most 4 per SM for heat and KS FP64 states.  A
  *                        streamed launch takes at most the resident warps and
  *                        at most N/B/3 (3 windows per warp or more).
  *   SWEPT_OPT_GRAPH      1: swept_advance captures its stage sequence into a
@@ -271,7 +271,8 @@ int swept_plan_status(swept_plan_t plan, void *stream);
 
 /*
  * swept_plan_last_advance -- what the plan's last swept_advance enqueued:
- * the kernel launches (stages; a streamed ring launch counts once) in
+ * the kernel launches (stages; a streamed ring launch and a cluster-resident
+ * advance, SWEPT_OPT_RESIDENT, count once) in
  * *launches, the ring launches among them in *ring_launches, and, when
  * SWEPT_OPT_TIME_RING is on and the advance was not captured, the device time
  * from the first ring launch's start to the last one's end in *ring_ms

@@ -480,7 +480,8 @@ swept_stream_kernel(const StageArgs a, int nwarps) {
 
 // Launch with `nwarps` warps; 0 picks min(resident warp slots of the GPU,
 // nwin / 2), so that every warp streams at least two windows when it can,
-// and for FP64 states at most one warp per scheduler (4 per SM).
+// and for the scalar stencils' FP64 states at most one warp per scheduler
+// (4 per SM).
 // nwarps < 0 is the automatic choice of kernel.  With at most one window per
 // scheduler (nwin <= 4 x SMs) every warp runs alone on its scheduler and the
 // stage time is one warp's chain of levels: the per-window kernel (2h levels)
@@ -488,12 +489,15 @@ swept_stream_kernel(const StageArgs a, int nwarps) {
 // is launched instead.  With more windows the pipes are shared and total work
 // decides: the ring computes (n+1) h (K+r) slot-levels per n windows against
 // 2h K for the per-window kernel, so the ring runs (as for 0).
-// FP64 states run on GB300's narrow FP64 pipe: one warp per scheduler already
-// keeps it busy, and fewer, longer ring runs waste fewer fill and drain slots.
+// FP64 states of the scalar stencils run on GB300's narrow FP64 pipe: one
+// warp per scheduler already keeps it busy, and fewer, longer ring runs waste
+// fewer fill and drain slots.  Not the Euler equations' FP64 state: its face
+// flux is a long chain through divisions and square roots that one warp per
+// scheduler leaves the pipe waiting on (measured on GB300, N = 2^23, B = 64:
+// 8.5e8 cell-steps/s with one block per SM, 9.4e8 with three).
 template <class DT> struct FP64Pipe { static constexpr bool value = false; };
 template <> struct FP64Pipe<F64> { static constexpr bool value = true; };
 template <> struct FP64Pipe<F64P> { static constexpr bool value = true; };
-template <> struct FP64Pipe<F64E> { static constexpr bool value = true; };
 
 template <int ST, class DT, int K>
 cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
