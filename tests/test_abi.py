@@ -101,3 +101,16 @@ def test_binding_fails_loudly_without_library(tmp_path):
             sw.load(str(tmp_path / "missing.so"))
         finally:
             sw._lib = None
+
+
+def test_binding_constants_match_the_header():
+    """Every SWEPT_* integer constant of the binding has the value include/swept.h defines."""
+    text = open(os.path.join(ROOT, "include", "swept.h")).read()
+    defined = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(SWEPT_\w+)\s+(-?\d+)\b", text)}
+    assert {"SWEPT_OPT_RESIDENT", "SWEPT_OPT_NAIVE_RESIDENT", "SWEPT_OPT_STREAM"} <= set(defined)
+    checked = 0
+    for name, value in defined.items():
+        if hasattr(sw, name):
+            assert getattr(sw, name) == value, name
+            checked += 1
+    assert checked >= 20
