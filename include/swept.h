@@ -109,7 +109,7 @@ typedef struct swept_plan_s *swept_plan_t;
  * Defines the problem of Section 3: a periodic 1D grid of N points split
  * into N/B tiles of B points, each advanced by the stencil `stencil_id`
  * (radius `radius`, parameters `params[0..nparams)`) in arithmetic `dtype`.
- *   N       >= B, N % B == 0; or (K <= 16; Euler equations K <= 4 in FP64,
+ *   N       >= B, N % B == 0; or (Euler equations K <= 4 in FP64,
  *           8 compensated) any N at least nwide = ceil((N mod B)/(32 radius))
  *           tiles long: the last nwide windows are then wider than B (uneven
  *           tiles: their trapezoids keep the height h, their Vs stay B wide),

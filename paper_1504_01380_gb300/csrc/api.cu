@@ -154,13 +154,13 @@ bool use_ring(const swept_plan_s* p) {
 // Uneven tiles: N = nreg*B + (nwide - 1)*(B + 32r) + W with
 // nwide = ceil((N mod B) / (32r)) and the last window W = N - (its start)
 // points wide (B + 1 .. B + 32r), nreg >= 0, for every stencil and precision
-// the plan takes with K <= 16 (Euler equations: K <= 4 in FP64, 8
+// the plan takes (K <= 32; Euler equations: K <= 4 in FP64, 8
 // compensated).  Any N of at least nwide tiles is tiled so.  Returns nreg, or
 // -1 when N cannot be tiled so.
 int64_t uneven_nreg(int64_t N, int B, int radius, int stencil, int dtype) {
   if (stencil == SWEPT_EULER) {
     if (B / 32 > (dtype == SWEPT_F64 ? 4 : 8)) return -1;
-  } else if (B / 32 > 16) {
+  } else if (B / 32 > 32) {
     return -1;
   }
   const int64_t extra = N % B;

@@ -229,7 +229,7 @@ cudaError_t launch_naive_rk2(int stencil, int sub, const double* u, const double
 // Uneven tiles (N not a multiple of B): the last nwin - nreg windows are
 // B + 32r wide.  One warp per wide window does its V (a regular B window
 // centred on the previous stage's boundary, stored flat to u) and then its
-// trapezoid of the full width from u.  K in {1, 2, 4, 8, 16} (multiple of r;
+// trapezoid of the full width from u.  K in {1, 2, 4, 8, 16, 32} (multiple of r;
 // Euler equations: K <= 4 in FP64, K <= 8 compensated).  ring < 0 launches
 // the wide windows alone; ring >= 0 a full diamond stage in one launch, the
 // ring over the a.nlaunch = nreg regular windows with `ring` warps (0:
@@ -239,7 +239,7 @@ cudaError_t launch_wide_f32c(int stencil, int K, const StageArgs& a, int nreg, i
 cudaError_t launch_wide_f32(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s, int ring);
 cudaError_t launch_wide_rk2(int stencil, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s, int ring);
 cudaError_t launch_wide_euler(int dtype, int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
-// The transposed KS step (adjoint sweeps) on the wide windows, FP64, K in {2, 4, 8, 16}.
+// The transposed KS step (adjoint sweeps) on the wide windows, FP64, K in {2, 4, 8, 16, 32}.
 cudaError_t launch_wide_ksadj(int K, const StageArgs& a, int nreg, int odd, cudaStream_t s);
 
 // Persistent advance (every stage in one launch, windows synchronised by

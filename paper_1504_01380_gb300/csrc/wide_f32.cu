@@ -12,6 +12,7 @@ cudaError_t launch_wide_dt(int stencil, int K, const StageArgs& a, int nreg, int
       case 4: return launch_wk<kHeat, DT, 4, 5>(a, nreg, odd, s, ring);
       case 8: return launch_wk<kHeat, DT, 8, 9>(a, nreg, odd, s, ring);
       case 16: return launch_wk<kHeat, DT, 16, 17>(a, nreg, odd, s, ring);
+      case 32: return launch_wk<kHeat, DT, 32, 33>(a, nreg, odd, s, ring);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -20,6 +21,7 @@ cudaError_t launch_wide_dt(int stencil, int K, const StageArgs& a, int nreg, int
     case 4: return launch_wk<kKS, DT, 4, 6>(a, nreg, odd, s, ring);
     case 8: return launch_wk<kKS, DT, 8, 10>(a, nreg, odd, s, ring);
     case 16: return launch_wk<kKS, DT, 16, 18>(a, nreg, odd, s, ring);
+    case 32: return launch_wk<kKS, DT, 32, 34>(a, nreg, odd, s, ring);
     default: return cudaErrorInvalidValue;
   }
 }

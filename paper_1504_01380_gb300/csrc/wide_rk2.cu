@@ -10,6 +10,7 @@ cudaError_t launch_wide_rk2(int stencil, int K, const StageArgs& a, int nreg, in
       case 4: return launch_wk<kHeatRK2, F64P, 4, 5>(a, nreg, odd, s, ring);
       case 8: return launch_wk<kHeatRK2, F64P, 8, 9>(a, nreg, odd, s, ring);
       case 16: return launch_wk<kHeatRK2, F64P, 16, 17>(a, nreg, odd, s, ring);
+      case 32: return launch_wk<kHeatRK2, F64P, 32, 33>(a, nreg, odd, s, ring);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -18,6 +19,7 @@ cudaError_t launch_wide_rk2(int stencil, int K, const StageArgs& a, int nreg, in
     case 4: return launch_wk<kKSRK2, F64P, 4, 6>(a, nreg, odd, s, ring);
     case 8: return launch_wk<kKSRK2, F64P, 8, 10>(a, nreg, odd, s, ring);
     case 16: return launch_wk<kKSRK2, F64P, 16, 18>(a, nreg, odd, s, ring);
+    case 32: return launch_wk<kKSRK2, F64P, 32, 34>(a, nreg, odd, s, ring);
     default: return cudaErrorInvalidValue;
   }
 }

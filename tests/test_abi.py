@@ -58,6 +58,7 @@ def _plan_rc(lib, N, radius, stencil, params, dtype, B):
     (1280, 1, 0, [0.25], 0, 512, -1),       # uneven tiles would need 8 wide windows out of 2
     (100, 2, 1, [0.002, 0.5], 0, 128, -1),  # KS: shorter than one 128-point tile
     (1000, 1, 0, [0.25], 0, 512, -1),       # 1 tile of 512 with 488 left: needs 16 wide windows
+    (2000, 1, 0, [0.25], 0, 1024, -1),      # 1 tile of 1024 with 976 left: needs 31 wide windows
     (1024, 2, 0, [0.25], 0, 32, -1),        # radius does not match heat
     (1024, 1, 1, [0.002, 0.5], 0, 64, -1),  # radius does not match KS
     (1024, 2, 1, [0.002, 0.5], 0, 32, -1),  # KS needs K % 2 == 0

@@ -17,7 +17,7 @@ def layouts(B, r):
     return [(n, w) for n, w in ((0, 1), (1, 1), (5, 1), (3, 2), (9, 4)) if w * 32 * r < B or w == 1 and n == 0]
 
 
-CASES = [(st, dt, B, nreg, nwide) for st in (HEAT, KS) for dt in (F64, F32C, F32) for B in (32, 64, 128, 512)
+CASES = [(st, dt, B, nreg, nwide) for st in (HEAT, KS) for dt in (F64, F32C, F32) for B in (32, 64, 128, 512, 1024)
          if (B // 32) % (1 if st == HEAT else 2) == 0
          for nreg, nwide in layouts(B, 1 if st == HEAT else 2)]
 
@@ -104,7 +104,8 @@ def test_any_n_runge_kutta_and_euler(cuda_lib):
 
 
 @pytest.mark.parametrize("N,B,ring", [(128 + 192, 128, False), (1009, 128, False), (20 * 128 + 3 * 192 + 77, 128, True),
-                                      (13 * 256 + 101, 256, True), (64 * 40 + 31, 64, False)])
+                                      (13 * 256 + 101, 256, True), (64 * 40 + 31, 64, False),
+                                      (9 * 1024 + 130, 1024, True)])
 def test_uneven_adjoint_matches_oracle(cuda_lib, N, B, ring):
     """The KS adjoint on uneven tiles of any N: the forward pass's checkpoints come from the
     regular windows' kernels and from the wide windows' trapezoid loads, the transposed sweep
@@ -134,7 +135,8 @@ def test_uneven_adjoint_matches_oracle(cuda_lib, N, B, ring):
 # choice of kernel, 0 = ring with automatic warps)
 JOINT = [(HEAT, F64, 128, 128 * 25 + 100, 3), (HEAT, F32C, 128, 128 * 12 + 33, 0), (HEAT, F32, 64, 64 * 15 + 7, 2),
          (KS, F64, 128, 128 * 20 + 100, 4), (KS, F32C, 512, 512 * 12 + 300, 3), (KS, F32, 256, 256 * 10 + 130, 0),
-         (HEAT, F32C, 32, 32 * 700 + 7, None), (KS, F32C, 64, 64 * 700 + 50, None)]
+         (HEAT, F32C, 32, 32 * 700 + 7, None), (KS, F32C, 64, 64 * 700 + 50, None),
+         (HEAT, F32C, 1024, 1024 * 12 + 100, 3), (KS, F64, 1024, 1024 * 10 + 200, 0)]
 
 
 @pytest.mark.parametrize("stencil,dtype,B,N,warps", JOINT)
