@@ -22,7 +22,10 @@ alternation makes that exact with one message per stage:
   the right neighbour, which holds the left neighbour's in return.
 
 Nothing else crosses a slice boundary: every other window of every stage lies
-inside its slice.  Per stage a rank sends B edge elements to one neighbour
+inside its slice.  The FP64 reductions (the sum, J = 1/2 sum u^2, <g, v>) are the
+one collective: each rank reduces its slice and the ranks all-gather the
+partials, which every rank adds with one rounding (``sharded_reduce``), so all
+ranks hold the same bits whatever the order the partials arrive in.  Per stage a rank sends B edge elements to one neighbour
 (8 KB for FP64 at B = 1024), so the network latency is paid once per h
 sub-timesteps (Section 4, Eq. 1).  No collective and no load from another
 GPU's memory is needed: on GPUs the messages are NCCL send/recv pairs.
@@ -227,6 +230,39 @@ class TorchDistTransport:
         works = [dist.isend(send_buf, dst, group=self.group, tag=tag),
                  dist.irecv(recv_buf, src, group=self.group, tag=tag)]
         return _TorchHandle(works)
+
+
+# ---------------------------------------------------------------- reductions
+def combine_partials(partials) -> float:
+    """The sum of per-rank FP64 partials rounded once (math.fsum: the exact sum of the
+    partials, correctly rounded), so the result does not depend on their order."""
+    import math
+    return math.fsum(float(p) for p in partials)
+
+
+class TorchDistReducer:
+    """All-gather of one FP64 partial per rank (gloo on CPU tensors, NCCL on CUDA tensors),
+    combined by ``combine_partials`` on every rank.  The all-gather is bounded by the process
+    group's timeout."""
+
+    def __init__(self, group=None):
+        self.group = group
+
+    def allreduce(self, partial) -> float:
+        import torch
+        import torch.distributed as dist
+        world = dist.get_world_size(self.group)
+        parts = [torch.empty_like(partial) for _ in range(world)]
+        dist.all_gather(parts, partial, group=self.group)
+        return combine_partials(t.item() for t in parts)
+
+
+def sharded_reduce(plan, u, what: int, reducer, v=None, stream=None) -> float:
+    """An FP64 reduction (SWEPT_SUM, SWEPT_HALF_SUMSQ, SWEPT_DOT with ``v`` the rank's slice of
+    the other vector) of a field sharded over ranks: the slice's partial by swept_reduce on
+    the slice's plan, then ``reducer.allreduce``."""
+    from . import swept_reduce
+    return reducer.allreduce(swept_reduce(plan, u, what, v, stream=stream))
 
 
 # ------------------------------------------------------------------ GPU runner

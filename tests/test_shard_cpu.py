@@ -103,11 +103,31 @@ def _worker(rank, world, port, q, mode):
             os._exit(0)
 
 
+def _reduce_worker(rank, world, port, q):
+    """Each rank's partials (exactly rounded sums of its slice, the stand-in for the slice's
+    swept_reduce), combined over the ranks by the product reducer."""
+    import math
+
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    N = world * 1000
+    u, v = workloads.uniform(N, 93), workloads.uniform(N, 94)
+    lo, hi = rank * 1000, (rank + 1) * 1000
+    red = shard.TorchDistReducer()
+    parts = [math.fsum(u[lo:hi]), 0.5 * math.fsum(u[lo:hi] ** 2), math.fsum(u[lo:hi] * v[lo:hi])]
+    got = [red.allreduce(torch.tensor([p], dtype=torch.float64)) for p in parts]
+    q.put((rank, got))
+    dist.destroy_process_group()
+
+
 def _spawn(world, mode, timeout=300):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, q, mode)) for r in range(world)]
+    target, args = (_reduce_worker, ()) if mode == "reduce" else (_worker, (mode,))
+    procs = [ctx.Process(target=target, args=(r, world, port, q) + args) for r in range(world)]
     for p in procs:
         p.start()
     res = dict(q.get(timeout=timeout) for _ in procs)
@@ -186,3 +206,28 @@ def test_slice_rejects_partial_tiles():
         shard.Slice(1000, 64, 3, 0)
     s = shard.Slice(3 * 4 * 64, 64, 3, 2)
     assert (s.n_local, s.nwin, s.start, s.left, s.right) == (256, 4, 512, 1, 0)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_reduction_same_bits_on_every_rank(world):
+    """The FP64 reductions of a sharded field: every rank holds the same bits, within one
+    rounding per rank of the exact sum (each partial rounded once, their sum rounded once)."""
+    import math
+    res = _spawn(world, "reduce")
+    N = world * 1000
+    u, v = workloads.uniform(N, 93), workloads.uniform(N, 94)
+    exact = [math.fsum(u), 0.5 * math.fsum(u ** 2), math.fsum(u * v)]
+    scale = [np.sum(np.abs(u)), 0.5 * np.sum(u ** 2), np.sum(np.abs(u * v))]
+    for r in range(world):
+        assert res[r] == res[0]
+    for g, e, sc in zip(res[0], exact, scale):
+        assert abs(g - e) <= (world + 1) * 2.0 ** -53 * sc
+
+
+def test_combine_partials_is_order_free():
+    rng = np.random.default_rng(5)
+    parts = list(rng.standard_normal(7) * 10.0 ** rng.integers(-8, 8, 7))
+    want = shard.combine_partials(parts)
+    for _ in range(5):
+        rng.shuffle(parts)
+        assert shard.combine_partials(parts) == want

@@ -161,3 +161,48 @@ def test_sharded_runge_kutta_and_euler(cuda_lib):
             glo = a[3 * n:].reshape(3, n).T
             assert np.array_equal(ghi, whi[rank * n:(rank + 1) * n]), (nsteps, rank)
             assert np.array_equal(glo, wlo[rank * n:(rank + 1) * n]), (nsteps, rank)
+
+
+class _LocalReducer:
+    """The all-gather of a sharded reduction, for slices of one process: the partials are
+    collected, then combined as the product reducer combines them."""
+
+    def __init__(self):
+        self.parts = []
+
+    def allreduce(self, partial):
+        self.parts.append(partial.item())
+        return shard.combine_partials(self.parts)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_sharded_reduction_matches_whole_field(cuda_lib, dtype):
+    """sharded_reduce over 4 slices of one field (each slice's swept_reduce, combined once)
+    against the oracle's exactly rounded sums: within the single-field bound plus one
+    rounding per slice."""
+    import torch
+    from oracle import reductions as ored
+    sw = cuda_lib
+    world, B, N = 4, 256, 4 * 256 * 64
+    u0, v = workloads.heat_noise_modes(N, 16, 4), workloads.uniform(N, 6)
+    vals = u0 if dtype == 0 else oracle.merge_f32c(*oracle.split_f32c(u0))
+    got = {}
+    for what in (sw.SWEPT_SUM, sw.SWEPT_HALF_SUMSQ, sw.SWEPT_DOT):
+        red = _LocalReducer()
+        for rank in range(world):
+            sl = shard.Slice(N, B, world, rank)
+            plan = sw.swept_plan(sl.n_local, 1, 0, [0.25], dtype, B)
+            seg = u0[sl.start:sl.start + sl.n_local]
+            if dtype == 0:
+                u = torch.tensor(seg, device="cuda")
+            else:
+                hi, lo = oracle.split_f32c(seg)
+                u = torch.tensor(np.concatenate([hi, lo]), device="cuda")
+            vv = torch.tensor(v[sl.start:sl.start + sl.n_local], device="cuda")
+            got[what] = shard.sharded_reduce(plan, u, what, red, v=vv if what == sw.SWEPT_DOT else None)
+            plan.destroy()
+    eps = np.finfo(np.float64).eps
+    for what, ex, scale in ((sw.SWEPT_SUM, ored.total(vals), np.sum(np.abs(vals))),
+                            (sw.SWEPT_HALF_SUMSQ, ored.half_sumsq(vals), ored.half_sumsq(vals)),
+                            (sw.SWEPT_DOT, ored.dot(vals, v), np.sum(np.abs(vals * v)))):
+        assert abs(got[what] - ex) <= 4 * eps * abs(ex) + (world + N * eps) * eps * scale, (what, got[what], ex)
