@@ -189,11 +189,37 @@ def measured_hbm_gbs() -> float:
 
 
 # ------------------------------------------------- committed ncu figures
+def code_tokens(text: str) -> str:
+    """C++ source without its comments and with every run of whitespace made one space, so
+    that the digest of a file changes with its code only (string literals kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':                                  # string literal: copy to its closing quote
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_digest(names=HEADLINE_SOURCES) -> str:
+    """sha256 (16 hex digits) of the named kernel sources' code (comments and layout ignored)."""
     h = hashlib.sha256()
     for name in names:
-        with open(os.path.join(ROOT, "paper_1504_01380_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1504_01380_gb300", "csrc", name), encoding="utf-8") as f:
+            h.update(code_tokens(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -71,9 +71,16 @@ def test_traffic_only_from_a_capture_of_the_current_sources(monkeypatch, tmp_pat
     prof.write_text(f"source digest: `{digest}`\n" + body)
     t, note = bench.profile_traffic(str(prof), ("a.cuh",))
     assert t == 12.75e9 and "current" in note
+    (csrc / "a.cuh").write_text("kernel  v1 // a note\n/* and\n another */")  # comments only
+    assert bench.profile_traffic(str(prof), ("a.cuh",))[0] == 12.75e9
     (csrc / "a.cuh").write_text("kernel v2")                                  # the kernel changed
     t, note = bench.profile_traffic(str(prof), ("a.cuh",))
     assert t is None and "changed" in note
+
+
+def test_code_tokens_strips_comments_not_strings():
+    src = 'int a = 1; // one\n/* two\n lines */ const char* s = "// kept /* too */";\n  int  b;'
+    assert bench.code_tokens(src) == 'int a = 1; const char* s = "// kept /* too */"; int b;'
 
 
 def test_alu_peak_fallback_is_the_nominal_rate(monkeypatch, tmp_path):
