@@ -120,17 +120,19 @@ naive_step_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t N
 // counterpart of the cluster-resident swept advance): the field is split over
 // the C blocks, M = N / C points each, held in shared memory with R halo
 // points per side, [R halo | M own | R halo], in two buffers (hi then lo for
-// a compensated field).  Each step refreshes the halos from the neighbouring
-// blocks' own points through distributed shared memory, steps the padded
-// field (its own points need no wrap) into the other buffer, and ends with a
-// cluster barrier: one barrier per sub-timestep where the swept advance
-// needs one per stage.
+// a compensated field).  Each step steps the padded field (its own points
+// need no wrap) into the other buffer, then pushes its first and last R own
+// points into the neighbouring blocks' halo inboxes through distributed
+// shared memory, and ends with a cluster barrier; the next step starts by
+// copying its inbox into its halo.  One barrier per sub-timestep where the
+// swept advance needs one per stage.
 template <int ST, class DT>
 __global__ void __launch_bounds__(1024, 1)
 naive_cluster_kernel(void* __restrict__ u, int64_t N, const Consts c, int64_t nsteps, int M) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int R = Radius<ST>::value;
   constexpr int NC = std::is_same<DT, F32C>::value ? 2 : 1;   // components (hi, lo)
+  constexpr int NH = 2 * R * NC;                             // halo values per block
   using Cc = typename DT::C;
   cg::cluster_group cl = cg::this_cluster();
   griddep_wait();
@@ -138,25 +140,40 @@ naive_cluster_kernel(void* __restrict__ u, int64_t N, const Consts c, int64_t ns
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int left = (rank + C - 1) % C, right = (rank + 1) % C;
   Cc* buf[2] = {reinterpret_cast<Cc*>(smem_raw), reinterpret_cast<Cc*>(smem_raw) + NC * L};
+  // inbox[p][j * 2R + q]: halo point q of component j (q < R: left halo, else right),
+  // written by the neighbours at the end of the step before one of parity p
+  Cc* inbox[2] = {buf[1] + NC * L, buf[1] + NC * L + NH};
   const int64_t g0 = (int64_t)rank * M;
   Cc* uc = static_cast<Cc*>(u);
   for (int i = threadIdx.x; i < M; i += blockDim.x)
 #pragma unroll
     for (int j = 0; j < NC; ++j) buf[0][j * L + R + i] = uc[j * N + g0 + i];
   cl.sync();                                                 // every block started and loaded
-  const int64_t i0 = (int64_t)threadIdx.x * kV;
+  const int tid = threadIdx.x;
+  const int jh = tid / (2 * R), qh = tid % (2 * R);         // this thread's halo value (tid < NH)
+  if (tid < NH) {
+    // step 0's halo, read from the neighbours once: the left block's own points M - R + q
+    // (its buf[0][M + q]), the right block's own points q (its buf[0][R + q])
+    Cc* b0 = buf[0];
+    if (qh < R) b0[jh * L + qh] = *cl.map_shared_rank(b0 + jh * L + M + qh, (unsigned)left);
+    else b0[jh * L + M + qh] = *cl.map_shared_rank(b0 + jh * L + qh, (unsigned)right);
+  }
+  const int64_t i0 = (int64_t)tid * kV;
   for (int64_t k = 0; k < nsteps; ++k) {
     Cc* cur = buf[k & 1];
-    if (threadIdx.x < 2 * R * NC) {
-      // halo point q of component j: the left block's own points M - R + q (its
-      // cur[M + q]), the right block's own points q (its cur[R + q])
-      const int j = threadIdx.x / (2 * R), q = threadIdx.x % (2 * R);
-      if (q < R) cur[j * L + q] = *cl.map_shared_rank(cur + j * L + M + q, (unsigned)left);
-      else cur[j * L + M + q] = *cl.map_shared_rank(cur + j * L + q, (unsigned)right);
-    }
+    Cc* nxt = buf[(k + 1) & 1];
+    if (k > 0 && tid < NH) cur[jh * L + (qh < R ? qh : M + qh)] = inbox[k & 1][tid];
     __syncthreads();
-    naive_points<ST, DT>(cur, buf[(k + 1) & 1], L, c, i0, threadIdx.x & 31);
-    cl.sync();                                               // this step's points, read as halos next
+    naive_points<ST, DT>(cur, nxt, L, c, i0, tid & 31);
+    __syncthreads();
+    if (tid < NH) {
+      // my first R own points go to the left block's right halo (its q = R + q'), my last R
+      // own points to the right block's left halo (its q = q')
+      Cc* box = inbox[(k + 1) & 1];
+      if (qh < R) *cl.map_shared_rank(box + jh * 2 * R + R + qh, (unsigned)left) = nxt[jh * L + R + qh];
+      else *cl.map_shared_rank(box + jh * 2 * R + qh - R, (unsigned)right) = nxt[jh * L + M + qh - R];
+    }
+    cl.sync();                                               // the halos are in the inboxes
   }
   const Cc* fin = buf[nsteps & 1];
   for (int i = threadIdx.x; i < M; i += blockDim.x)
@@ -372,7 +389,7 @@ cudaError_t launch_res(void* u, int64_t N, const Consts& c, int64_t nsteps, cuda
   const int C = naive_cluster_blocks(N, R);
   if (C == 0) return query ? cudaSuccess : cudaErrorInvalidValue;
   const int M = (int)(N / C), L = M + 2 * R;
-  const size_t smem = (size_t)2 * NC * L * sizeof(typename DT::C);
+  const size_t smem = (size_t)(2 * NC * L + 2 * 2 * R * NC) * sizeof(typename DT::C);   // fields, inboxes
   const int threads = ((L + kV - 1) / kV + 31) / 32 * 32;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);

@@ -1,8 +1,9 @@
 // Cluster-resident swept advance, for problems of at most 64 windows: the
 // whole advance in one launch of one thread block cluster (up to 16 blocks
-// on 16 SMs, one warp per window).  Each block keeps its windows' stage edges
-// in its shared memory; a window's V-fill reads its neighbours' edges through
-// distributed shared memory, and the stage boundary is a cluster barrier.  On
+// on 16 SMs, one warp per window).  At the end of a stage each window pushes
+// its two edge halves into the shared memory of the two windows of the next
+// stage that read them (through distributed shared memory), and the stage
+// boundary is a cluster barrier.  On
 // GB300 that barrier (with a remote shared-memory load) takes about 0.27 us,
 // where a stage boundary through global memory and a kernel launch costs
 // about 2.4 us (the latency tau of Eq. 1 on this GPU), and every window still
@@ -34,12 +35,13 @@ bool cluster_shape(int nwin, int& W, int& C) {
   return false;
 }
 
-// Shared memory per block: the edge double buffer of its W windows (2 x W x
-// 2B elements), each warp's two arms (3B elements: [B, 2B) left, [2B, 3B)
-// right; [0, B) unused) and the stage code's staging area (2B elements).
+// Shared memory per block, per warp: the stage's output edges (2B elements:
+// the left half, then the right), the arms of the next stage in two parity
+// buffers of 3B elements ([B, 2B) the left arm, [2B, 3B) the right; [0, B)
+// unused), and the stage code's staging area (2B elements).
 template <class DT>
 size_t cluster_smem(int W, int B) {
-  return (size_t)W * 9 * B * sizeof(typename DT::E);
+  return (size_t)W * 10 * B * sizeof(typename DT::E);
 }
 
 template <int ST, class DT, int K>
@@ -54,40 +56,45 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 1) swept_cluster_kernel(c
   const int wi = threadIdx.x >> 5;                          // this warp's window in the block
   const int w = (int)cl.block_rank() * W + wi;              // window index
   const int nwin = p.a.nwin;
-  E* ebuf = reinterpret_cast<E*>(smem_raw);                 // [2][W][2B]
-  E* arms = ebuf + (size_t)4 * W * B + (size_t)wi * 3 * B;
-  E* sm = ebuf + (size_t)7 * W * B + (size_t)wi * 2 * B;
+  E* base = reinterpret_cast<E*>(smem_raw);
+  E* eout = base + (size_t)wi * 2 * B;                      // [W][2B]
+  E* arms0 = base + (size_t)2 * W * B;                      // [2][W][3B]
+  E* sm = base + (size_t)8 * W * B + (size_t)wi * 2 * B;    // [W][2B]
   StageArgs a = p.a;
   for (int k = 0; k < p.nstages; ++k) {
     stage_shape(k, p.q, p.rem, p.H, a.hv, a.ht);
     a.offset = (k & 1) ? B / 2 : 0;
     a.lev_fill = k >= 1 ? (int64_t)(k - 1) * p.H : 0;
     a.lev_trap = (int64_t)k * p.H;
-    if (a.hv > 0) {
-      // the V's arms: the right edges of window wl and the left edges of window wr of
-      // stage k - 1, in the blocks that hold them
-      const int wl = a.offset ? w : (w == 0 ? nwin - 1 : w - 1);
-      const int wr = a.offset ? (w + 1 == nwin ? 0 : w + 1) : w;
-      const E* prev = ebuf + (size_t)((k + 1) & 1) * W * 2 * B;
-      const uint4* srcL = reinterpret_cast<const uint4*>(
-          cl.map_shared_rank(prev + (size_t)(wl % W) * 2 * B + B, (unsigned)(wl / W)));
-      const uint4* srcR = reinterpret_cast<const uint4*>(
-          cl.map_shared_rank(prev + (size_t)(wr % W) * 2 * B, (unsigned)(wr / W)));
-      uint4* dL = reinterpret_cast<uint4*>(arms + B);
-      uint4* dR = reinterpret_cast<uint4*>(arms + 2 * B);
-      const int n16 = (a.hv * 2 * R * (int)sizeof(E) + 15) / 16;
-      for (int i = lane; i < n16; i += 32) {
-        dL[i] = srcL[i];
-        dR[i] = srcR[i];
-      }
-      __syncwarp();
-    }
-    // the stage code reads its arms at windows 0 (right half) and 1 (left half) of
-    // a.ein and writes its edges to window 0 of a.eout
-    a.ein = arms;
-    a.eout = ebuf + (size_t)(k & 1) * W * 2 * B + (size_t)wi * 2 * B;
+    // the stage code reads its arms at windows 0 (right half) and 1 (left half) of a.ein,
+    // pushed here by the windows that computed them, and writes its edges to window 0 of
+    // a.eout
+    a.ein = arms0 + (size_t)(k & 1) * W * 3 * B + (size_t)wi * 3 * B;
+    a.eout = eout;
     StageImpl<ST, DT, K>::run_window_at(a, sm, (int64_t)w * B + a.offset, 0, 1, 0, B, false);
-    cl.sync();                                                 // stage k's edges, read by stage k + 1
+    if (a.ht > 0 && k + 1 < p.nstages) {
+      // push the edges to the windows of stage k + 1 that read them: at an offset stage
+      // window v reads windows v and v + 1 of stage k, at an unshifted one v - 1 and v; so
+      // the right edges go to the left arm of window w (next stage offset) or w + 1, the left
+      // edges to the right arm of window w - 1 or w
+      __syncwarp();
+      const bool next_offset = ((k + 1) & 1) != 0;
+      const int vr = next_offset ? w : (w + 1 == nwin ? 0 : w + 1);
+      const int vl = next_offset ? (w == 0 ? nwin - 1 : w - 1) : w;
+      E* nxt = arms0 + (size_t)((k + 1) & 1) * W * 3 * B;
+      uint4* dR = reinterpret_cast<uint4*>(
+          cl.map_shared_rank(nxt + (size_t)(vr % W) * 3 * B + B, (unsigned)(vr / W)));
+      uint4* dL = reinterpret_cast<uint4*>(
+          cl.map_shared_rank(nxt + (size_t)(vl % W) * 3 * B + 2 * B, (unsigned)(vl / W)));
+      const uint4* sR = reinterpret_cast<const uint4*>(eout + B);
+      const uint4* sL = reinterpret_cast<const uint4*>(eout);
+      const int n16 = (a.ht * 2 * R * (int)sizeof(E) + 15) / 16;
+      for (int i = lane; i < n16; i += 32) {
+        dR[i] = sR[i];
+        dL[i] = sL[i];
+      }
+    }
+    cl.sync();                                                 // stage k's edges are in the arms
   }
 }
 
