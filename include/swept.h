@@ -172,7 +172,9 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        A wait that runs out ends the launch with the status
  *                        SWEPT_ETIMEOUT, read by swept_plan_status.
  *   SWEPT_OPT_STREAM     1 (default): an advance whose ring stages (full
- *                        diamonds on evenly tiled windows, forward schemes)
+ *                        diamonds, forward schemes; uneven tiles but for the
+ *                        Euler equations, with one warp per wide window beside
+ *                        the regular windows' runs and per-window counters)
  *                        number two or more runs them all in one cooperative
  *                        launch, where each warp's last slot of a stage is the
  *                        first slot of its next stage; warps then wait (bounded,
@@ -210,9 +212,10 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        barrier per step: the per-step counterpart of
  *                        SWEPT_OPT_RESIDENT); 0 (default): one launch per step.
  *   SWEPT_OPT_DROP_WINDOW failure injection: in the persistent advance window
- *                        `value`, in a streamed ring launch warp `value`, never
- *                        publishes its progress (a lost message), so the waits
- *                        on it run out; -1 (default) none.
+ *                        `value`, in a streamed ring launch warp `value` (of
+ *                        uneven tiles: window `value`), never publishes its
+ *                        progress (a lost message), so the waits on it run
+ *                        out; -1 (default) none.
  * Errors: SWEPT_EINVAL for an unknown option or value.
  */
 #define SWEPT_OPT_DIAMOND     0

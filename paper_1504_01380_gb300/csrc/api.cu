@@ -41,8 +41,8 @@ struct swept_plan_s {
   double timeout_s;       // SWEPT_OPT_TIMEOUT_MS / 1000: budget of each persistent or streamed wait
   int stream;             // SWEPT_OPT_STREAM: ring stages of an advance in one launch
   int time_ring;          // SWEPT_OPT_TIME_RING: events around the ring launches of each advance
-  int resident;           // SWEPT_OPT_RESIDENT: block-resident advance where the problem fits one block
-  int naive_resident;     // SWEPT_OPT_NAIVE_RESIDENT: the naive stepper's steps in one block
+  int resident;           // SWEPT_OPT_RESIDENT: cluster-resident advance where the problem fits one cluster
+  int naive_resident;     // SWEPT_OPT_NAIVE_RESIDENT: the naive stepper's steps in one cluster
   cudaEvent_t ring_ev[2];
   int ring_timed;         // the last advance recorded ring_ev
   int64_t last_launches, last_ring_launches;
@@ -452,22 +452,40 @@ long long wait_budget(const swept_plan_s* p) {
 // launch when there are at least two of them, the tiles are even, and the
 // ring is the kernel for them (with the automatic choice: more windows than
 // four per SM, where the per-window kernel is not picked instead).
+// Uneven tiles stream too (swept_stream_wide_kernel: the wide windows beside
+// the regular windows' runs), except for the Euler equations, whose wide
+// windows' shared memory would cost their ring a block per SM.
 bool stream_ok(const swept_plan_s* p, int64_t q) {
-  if (!p->stream || p->nreg != p->nwin || q < 3 || p->nwin < 3 || !use_ring(p)) return false;
+  if (!p->stream || q < 3 || p->nreg < 3 || !use_ring(p)) return false;
+  if (p->nreg != p->nwin && p->stencil == SWEPT_EULER) return false;
   if (q - 1 > (int64_t)0x7fffffff / p->nwin) return false;    // slot counters stay in int
   if (p->diamond == SWEPT_DIAMOND_AUTO && p->ring_warps == 0) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (p->nwin <= 4 * sms) return false;
+    if (p->nreg <= 4 * sms) return false;
     // and only where it pays (run length against residency; the ring launcher decides)
     StageArgs a{};
-    a.nwin = p->nwin;
+    a.nwin = p->nreg;
     a.nstream = (int)(q - 1);
     a.stream_query = 1;
     return launch_ring(p, a, nullptr) == cudaSuccess;
   }
   return true;
+}
+
+// The wide windows of an uneven tiling (swept_wide.cuh): alone (ring < 0),
+// beside the ring over the a.nlaunch regular windows in one launch (ring >= 0
+// warps, 0 automatic), or, with a.nstream > 1, every full diamond stage of the
+// advance in one streamed launch.
+cudaError_t launch_wide(const swept_plan_s* p, const StageArgs& a, int odd, cudaStream_t s, int ring) {
+  if (p->stencil == SWEPT_EULER) return swept::launch_wide_euler(p->dtype, p->K, a, p->nreg, odd, s);
+  if (p->stencil == SWEPT_HEAT_RK2) return swept::launch_wide_rk2(swept::kHeatRK2, p->K, a, p->nreg, odd, s, ring);
+  if (p->stencil == SWEPT_KS_RK2) return swept::launch_wide_rk2(swept::kKSRK2, p->K, a, p->nreg, odd, s, ring);
+  const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
+  if (p->dtype == SWEPT_F64) return swept::launch_wide_f64(st, p->K, a, p->nreg, odd, s, ring);
+  if (p->dtype == SWEPT_F32C) return swept::launch_wide_f32c(st, p->K, a, p->nreg, odd, s, ring);
+  return swept::launch_wide_f32(st, p->K, a, p->nreg, odd, s, ring);
 }
 
 // Flat checkpoints an advance stores on the way (the adjoint's forward pass):
@@ -576,18 +594,8 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s, co
       ++nlaunch;
     }
     if (e != cudaSuccess) return e;
-    const int ring = joint ? (w > 0 ? w : 0) : -1;
     a.nlaunch = joint ? p->nreg : 0;
-    if (p->stencil == SWEPT_EULER) e = swept::launch_wide_euler(p->dtype, p->K, a, p->nreg, odd, s);
-    else if (p->stencil == SWEPT_HEAT_RK2)
-      e = swept::launch_wide_rk2(swept::kHeatRK2, p->K, a, p->nreg, odd, s, ring);
-    else if (p->stencil == SWEPT_KS_RK2) e = swept::launch_wide_rk2(swept::kKSRK2, p->K, a, p->nreg, odd, s, ring);
-    else {
-      const int st = p->stencil == SWEPT_HEAT ? swept::kHeat : swept::kKS;
-      if (p->dtype == SWEPT_F64) e = swept::launch_wide_f64(st, p->K, a, p->nreg, odd, s, ring);
-      else if (p->dtype == SWEPT_F32C) e = swept::launch_wide_f32c(st, p->K, a, p->nreg, odd, s, ring);
-      else e = swept::launch_wide_f32(st, p->K, a, p->nreg, odd, s, ring);
-    }
+    e = launch_wide(p, a, odd, s, joint ? (w > 0 ? w : 0) : -1);
     a.nlaunch = 0;
     return e;
   };
@@ -610,7 +618,16 @@ int enqueue_advance(swept_plan_s* p, void* u, int64_t nsteps, cudaStream_t s, co
       e = cudaMemsetAsync(p->flags, 0, (size_t)p->nwin * sizeof(int), s);
       if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
       if (e == cudaSuccess && timing) e = cudaEventRecord(p->ring_ev[0], s);
-      if (e == cudaSuccess) e = launch_ring(p, a, s);
+      if (e == cudaSuccess) {
+        if (!uneven) {
+          e = launch_ring(p, a, s);
+        } else {
+          // the regular windows' runs and the wide windows in one launch; the
+          // counters are per window
+          const int w = (p->diamond == SWEPT_DIAMOND_AUTO && p->ring_warps == 0) ? 0 : p->ring_warps;
+          e = launch_wide(p, a, 1, s, w);
+        }
+      }
       if (e == cudaSuccess && timing) e = cudaEventRecord(p->ring_ev[1], s);
       a.nstream = 0;
       ++nlaunch;

@@ -17,6 +17,7 @@
 
 #include "swept_ring.cuh"
 #include "swept_stage.cuh"
+#include "swept_sync.cuh"
 
 namespace swept {
 
@@ -83,6 +84,135 @@ swept_ring_wide_kernel(const StageArgs a, int nwarps, int nreg, int odd) {
   }
 }
 
+// Every full diamond stage of an advance on uneven tiles in one cooperative
+// launch (a.nstream stages from the stage a describes).  Warps [0, nwarps)
+// stream drifting runs of the regular windows [0, nreg) through the ring, as
+// swept_stream_kernel does for even tiles (run indices modulo nreg, so a run
+// may step from window nreg - 1 to window 0, whose physical neighbours are
+// wide windows); the next nwin - nreg warps take one wide window each through
+// every stage.  Windows publish per-window stage counters (a.progress[w] =
+// streamed stages done, released after the window's edges are stored), and
+// every window waits, bounded, before its fill of stage j until the two
+// windows of stage j - 1 it reads from have published j: each wait is on an
+// earlier stage, so the waits end.  The same wait keeps the edge buffers
+// safe: a window's stage-j edges overwrite its stage-(j-2) edges, whose
+// readers at stage j - 1 are the very windows its stage-j fill waited for.
+
+// Bounded wait until window w has published `target` stages; false when the
+// budget ran out or another warp recorded a failure.
+__device__ __forceinline__ bool wait_window(const StageArgs& a, int w, int target) {
+  const long long t0 = clock64();
+  bool ok = true;
+  for (int it = 0;; ++it) {
+    if (ld_relaxed(a.progress + w) >= target) break;
+    if ((it & 63) == 63 && (clock64() - t0 > a.budget || ld_relaxed(a.status) != 0)) {
+      ok = false;
+      break;
+    }
+    __nanosleep(128);
+  }
+  fence_acq_rel();
+  return __all_sync(kFull, ok);
+}
+
+// (window a.drop never publishes: failure injection, a lost message)
+__device__ __forceinline__ void publish_window(const StageArgs& a, int w, int stages) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0 && w != a.drop) {
+    __threadfence();
+    st_release(a.progress + w, stages);
+  }
+}
+
+template <int ST, class DT, int K>
+__device__ bool stream_uneven_ring(const StageArgs& a, typename DT::E* sm, int g, int nwarps, int nreg) {
+  using RI = RingImpl<ST, DT, K>;
+  using E = typename DT::E;
+  constexpr int B = RI::B, H = RI::H;
+  const int lane = threadIdx.x & 31;
+  const int w0 = (int)(((int64_t)g * nreg) / nwarps);
+  const int n = (int)(((int64_t)(g + 1) * nreg) / nwarps) - w0;
+  if (n <= 0) return true;
+  const int odd0 = a.offset != 0;
+  E* s0 = sm;
+  E* s1 = sm + B;
+  Tile<DT, RI::S> t;
+  t.zero();
+  const int T = a.nstream * n;
+  int jf = 0, i_f = 0, je = 0, ie = 0;
+  for (int slot = 0; slot <= T; ++slot) {
+    const bool fill = slot < T;
+    const bool empty = slot > 0;
+    const int cl = (slot & 1) ? 16 : 0;
+    const bool offs = ((jf + odd0) & 1) != 0;
+    const int wf = (w0 + ((jf + odd0) >> 1) + i_f) % nreg;
+    if (fill) {
+      const int wl = offs ? wf : (wf == 0 ? a.nwin - 1 : wf - 1);
+      const int wr = offs ? (wf + 1 == a.nwin ? 0 : wf + 1) : wf;
+      if (jf > 0 && !(wait_window(a, wl, jf) && wait_window(a, wr, jf))) return false;
+      const E* ein = static_cast<const E*>((jf & 1) ? a.eout : a.ein);
+      RI::warp_copy(s0, ein + (int64_t)wl * (2 * B) + B, B, lane);
+      RI::warp_copy(s1, ein + (int64_t)wr * (2 * B), B, lane);
+    }
+    __syncwarp();
+    RI::slot_levels(t, a, s0, s1, lane, cl, fill, empty, a.lev_fill + (int64_t)jf * H, 0);
+    __syncwarp();
+    if (fill) RI::dump_fill(t, a, lane, cl, a.lev_trap / H + jf, (int64_t)wf * B + (offs ? B / 2 : 0));
+    if (empty) {
+      const int we = (w0 + ((je + odd0) >> 1) + ie) % nreg;
+      E* eout = static_cast<E*>((je & 1) ? const_cast<void*>(a.ein) : a.eout);
+      RI::warp_copy(eout + (int64_t)we * (2 * B), s0, B, lane);
+      RI::warp_copy(eout + (int64_t)we * (2 * B) + B, s1, B, lane);
+      publish_window(a, we, je + 1);
+      if (++ie == n) {
+        ie = 0;
+        ++je;
+      }
+    }
+    __syncwarp();
+    if (fill && ++i_f == n) {
+      i_f = 0;
+      ++jf;
+    }
+  }
+  return true;
+}
+
+template <int ST, class DT, int K, int KW>
+__device__ bool stream_uneven_wide(const StageArgs& a, typename DT::E* sm, int nreg, int i) {
+  constexpr int H = 32 * K / (2 * Radius<ST>::value);
+  const int jw = nreg + i;
+  const int odd0 = a.offset != 0;
+  for (int j = 0; j < a.nstream; ++j) {
+    const int odd = (j + odd0) & 1;
+    const int wl = odd ? jw : jw - 1;                          // jw >= nreg >= 1
+    const int wr = odd ? (jw + 1 == a.nwin ? 0 : jw + 1) : jw;
+    if (j > 0 && !(wait_window(a, wl, j) && wait_window(a, wr, j))) return false;
+    StageArgs aj = a;
+    aj.ein = (j & 1) ? a.eout : a.ein;
+    aj.eout = const_cast<void*>((j & 1) ? a.ein : static_cast<const void*>(a.eout));
+    aj.lev_fill = a.lev_fill + (int64_t)j * H;
+    aj.lev_trap = a.lev_trap + (int64_t)j * H;
+    wide_window<ST, DT, K, KW>(aj, sm, nreg, i, odd);
+    publish_window(a, jw, j + 1);
+  }
+  return true;
+}
+
+template <int ST, class DT, int K, int KW>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, RingBlocks<DT, KW>::value)
+swept_stream_wide_kernel(const StageArgs a, int nwarps, int nreg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using E = typename DT::E;
+  constexpr int BW = 32 * KW;
+  E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * BW);
+  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  bool ok = true;
+  if (gw < nwarps) ok = stream_uneven_ring<ST, DT, K>(a, sm, gw, nwarps, nreg);
+  else if (nreg + (gw - nwarps) < a.nwin) ok = stream_uneven_wide<ST, DT, K, KW>(a, sm, nreg, gw - nwarps);
+  if (!ok && (threadIdx.x & 31) == 0) atomicCAS(a.status, 0, SWEPT_ETIMEOUT);
+}
+
 // ring < 0: the wide windows alone (swept_wide_kernel).  ring >= 0: a full
 // diamond stage, the ring over the nreg = a.nlaunch regular windows with
 // `ring` warps (0: the resident warp slots less one per wide window, at most
@@ -101,6 +231,37 @@ cudaError_t launch_wk(const StageArgs& a, int nreg, int odd, cudaStream_t s, int
                          smem, s, a, nreg, odd);
   }
   if (nreg < 1) return cudaErrorInvalidValue;
+  if (a.nstream > 1) {
+    // every full diamond in one cooperative launch: every warp resident at once
+    cudaError_t e = cudaFuncSetAttribute(swept_stream_wide_kernel<ST, DT, K, KW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, swept_stream_wide_kernel<ST, DT, K, KW>,
+                                                      kWarpsPerBlock * 32, smem);
+    if (e != cudaSuccess) return e;
+    int resident = sms * per_sm * kWarpsPerBlock;
+    if (FP64Pipe<DT>::value && resident > 4 * sms) resident = 4 * sms;
+    int nwarps = ring > 0 ? ring : resident;
+    if (nwarps > nreg / 3) nwarps = nreg / 3;                // runs of at least 3 windows
+    if (ring == 0 && nwarps >= sms * kWarpsPerBlock) nwarps -= nwarps % (sms * kWarpsPerBlock);
+    if (nwarps + nwide > resident) nwarps = resident - nwide;  // the wide windows' warps
+    if (nwarps < 1) return cudaErrorInvalidValue;
+    const int grid = (nwarps + nwide + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kWarpsPerBlock * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, swept_stream_wide_kernel<ST, DT, K, KW>, a, nwarps, nreg);
+  }
   cudaError_t e = cudaFuncSetAttribute(swept_ring_wide_kernel<ST, DT, K, KW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

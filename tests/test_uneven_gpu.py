@@ -128,32 +128,37 @@ def test_uneven_adjoint_matches_oracle(cuda_lib, N, B, ring):
         assert np.array_equal(got, want), (N, B, nsteps, K, np.flatnonzero(got != want)[:8])
 
 
-# A full diamond stage of an uneven tiling on the ring runs the ring over the regular windows and
-# the wide windows in one launch (one warp per wide window beside the ring's runs): forced at small
-# N (the ring kernel with a few warps, or with its automatic warp count), automatic where the
-# regular windows outnumber four per SM.  (stencil, dtype, B, N, ring warps: None = automatic
-# choice of kernel, 0 = ring with automatic warps)
+# Full diamond stages of an uneven tiling on the ring: with SWEPT_OPT_STREAM every one of them in
+# one streamed launch (the regular windows' runs and one warp per wide window, per-window stage
+# counters), without it one launch per stage running the ring over the regular windows and the wide
+# windows together.  Forced at small N (the ring kernel with a few warps, or with its automatic
+# warp count), automatic where the regular windows outnumber four per SM.  (stencil, dtype, B, N,
+# ring warps: None = automatic choice of kernel, 0 = ring with automatic warps)
 JOINT = [(HEAT, F64, 128, 128 * 25 + 100, 3), (HEAT, F32C, 128, 128 * 12 + 33, 0), (HEAT, F32, 64, 64 * 15 + 7, 2),
          (KS, F64, 128, 128 * 20 + 100, 4), (KS, F32C, 512, 512 * 12 + 300, 3), (KS, F32, 256, 256 * 10 + 130, 0),
          (HEAT, F32C, 32, 32 * 700 + 7, None), (KS, F32C, 64, 64 * 700 + 50, None),
          (HEAT, F32C, 1024, 1024 * 12 + 100, 3), (KS, F64, 1024, 1024 * 10 + 200, 0)]
 
 
+@pytest.mark.parametrize("stream", [1, 0])
 @pytest.mark.parametrize("stencil,dtype,B,N,warps", JOINT)
-def test_uneven_joint_ring_and_wide_launch(cuda_lib, stencil, dtype, B, N, warps):
+def test_uneven_ring_and_wide_windows(cuda_lib, stencil, dtype, B, N, warps, stream):
     sw = cuda_lib
     r = 1 if stencil == HEAT else 2
     plan = sw.swept_plan(N, r, stencil, params_of(stencil), dtype, B)
     if warps is not None:
         sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
         sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, warps)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_STREAM, stream)
     h = plan.h
     u0 = initial(stencil, N, 9700 + N)
     for nsteps in (h + 1, 4 * h, 5 * h + h // 2 + 1):
         assert_same(plan, run_gpu(sw, plan, u0, nsteps), oracle_run(stencil, dtype, u0, nsteps))
-    # 5h + h/2 + 1 steps: the triangle, 4 diamonds (one launch each), the last V-fill with the
-    # remainder's trapezoid, and the remainder's V-fill (two launches for each of those three)
-    assert sw.swept_plan_last_advance(plan)[:2] == (4 + 3 * 2, 4)
+        assert sw.swept_plan_status(plan) == 0
+    # 5h + h/2 + 1 steps: the triangle, 4 diamonds, the last V-fill with the remainder's
+    # trapezoid and the remainder's V-fill (two launches for each of those three); the
+    # diamonds in one streamed launch, or one launch each
+    assert sw.swept_plan_last_advance(plan)[:2] == ((1 + 3 * 2, 1) if stream else (4 + 3 * 2, 4))
 
 
 def test_uneven_joint_launch_runge_kutta(cuda_lib):
@@ -170,3 +175,25 @@ def test_uneven_joint_launch_runge_kutta(cuda_lib):
         u0 = rk2_initial(st, N, 9800 + N)
         for nsteps in (per + 1, 4 * per + 3):
             assert np.array_equal(rk2_run(sw, plan, u0, nsteps), oracle.advance_rk2_f64(st, prm(st), u0, nsteps))
+
+
+def test_uneven_streamed_lost_window_times_out(cuda_lib):
+    """A window of the streamed uneven launch that never publishes (SWEPT_OPT_DROP_WINDOW, here
+    a wide one and a regular one) makes its readers' bounded waits run out: the advance reports
+    SWEPT_ETIMEOUT, and the next advance on the same plan, without the fault, is bit-exact."""
+    sw = cuda_lib
+    N, B = 128 * 20 + 100, 128
+    plan = sw.swept_plan(N, 1, HEAT, params_of(HEAT), F32C, B)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_DIAMOND, sw.SWEPT_DIAMOND_RING)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_RING_WARPS, 3)
+    sw.swept_plan_set(plan, sw.SWEPT_OPT_TIMEOUT_MS, 100)
+    u0 = initial(HEAT, N, 9900)
+    nsteps = 6 * plan.h + 3
+    nwin = N // B
+    for drop in (nwin - 1, 5):
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_DROP_WINDOW, drop)
+        run_gpu(sw, plan, u0, nsteps)
+        assert sw.swept_plan_status(plan) == sw.SWEPT_ETIMEOUT
+        sw.swept_plan_set(plan, sw.SWEPT_OPT_DROP_WINDOW, -1)
+        assert_same(plan, run_gpu(sw, plan, u0, nsteps), oracle_run(HEAT, F32C, u0, nsteps))
+        assert sw.swept_plan_status(plan) == 0
