@@ -178,6 +178,11 @@ __device__ bool stream_uneven_ring(const StageArgs& a, typename DT::E* sm, int g
   return true;
 }
 
+// Wide window nreg + i through every stage, by one warp.  (A wide window's
+// per-window work measured 2.4-2.7 ring slots: one warp per wide window keeps
+// it well within a ring run; giving a warp several wide windows to lend the
+// freed places to the ring measured slower, and a loop over them cost the
+// kernel registers, hence a block per SM.)
 template <int ST, class DT, int K, int KW>
 __device__ bool stream_uneven_wide(const StageArgs& a, typename DT::E* sm, int nreg, int i) {
   constexpr int H = 32 * K / (2 * Radius<ST>::value);
@@ -247,7 +252,8 @@ cudaError_t launch_wk(const StageArgs& a, int nreg, int odd, cudaStream_t s, int
     int nwarps = ring > 0 ? ring : resident;
     if (nwarps > nreg / 3) nwarps = nreg / 3;                // runs of at least 3 windows
     if (ring == 0 && nwarps >= sms * kWarpsPerBlock) nwarps -= nwarps % (sms * kWarpsPerBlock);
-    if (nwarps + nwide > resident) nwarps = resident - nwide;  // the wide windows' warps
+    if (nwarps < 1) return cudaErrorInvalidValue;
+    if (nwarps + nwide > resident) nwarps = resident - nwide;  // one warp per wide window
     if (nwarps < 1) return cudaErrorInvalidValue;
     const int grid = (nwarps + nwide + kWarpsPerBlock - 1) / kWarpsPerBlock;
     cudaLaunchConfig_t cfg = {};
