@@ -36,7 +36,9 @@ run.  On one GPU the line also carries:
                    ks_rk2_f1    KS by the two-stage Runge-Kutta rule (Section 6's
                                 initial condition), N = 2^22;
                    euler_f2     the Euler equations (Section 7), N = 2^23 and the
-                                4096-cell latency regime.
+                                4096-cell latency regime;
+                   uneven_f4    heat on N = 2^24 + 224 (uneven tiles) against
+                                N = 2^24, compensated FP32, B = 512.
 Algorithmic counts follow the hot-path scope's figures: compensated FP32
 heat 11 and KS 22 operations per cell-update against the measured FP32
 instruction rate (an add, mul or fma is one operation); FP64 heat 5 and KS 16
@@ -590,7 +592,7 @@ def run_reports(peaks, dev, flush) -> dict:
     for name, fn in (("heat_c1_f64", report_heat_f64), ("latency_c0", report_latency_c0),
                      ("ks_c2", report_ks_c2), ("batch_c3", report_batch_c3),
                      ("adjoint_c4", report_adjoint_c4), ("ks_rk2_f1", report_ks_rk2_f1),
-                     ("euler_f2", report_euler_f2)):
+                     ("euler_f2", report_euler_f2), ("uneven_f4", report_uneven_f4)):
         t0 = time.perf_counter()
         try:
             out[name] = fn(peaks, flush)
@@ -637,6 +639,41 @@ def report_heat_f64(peaks, flush):
                                  kernel="swept_stream_kernel<heat,f64,K=32>", avg_launch_ms=ring_ms / max(1, n_ring),
                                  flop_per_update=work, executed_ops_per_update=EXEC_OPS_F64["heat"],
                                  naive_frac=work * N_POINTS * NSTEPS / t_nv / peak if peak else None)}
+
+
+def report_uneven_f4(peaks, flush):
+    """Arbitrary N: the headline scheme (heat, compensated FP32, B = 512, 5000 steps) on
+    N = 2^24 + 224 (seven wide windows of 544 points) against the even N = 2^24, both with their
+    diamonds in one streamed launch; the uneven result against the naive stepper bit for bit."""
+    import torch
+    import paper_1504_01380_gb300 as sw
+    nsteps, B = 5000, 512
+    out = {}
+    for name, n in (("even", N_POINTS), ("uneven", N_POINTS + 224)):
+        u0 = sw.swept_f32c_split(torch.tensor(workloads.uniform(n, 5), device="cuda"))
+        u = u0.clone()
+        plan = sw.swept_plan(n, 1, sw.SWEPT_HEAT, [HEAT_R], sw.SWEPT_F32C, B)
+
+        def run(fn):
+            u.copy_(u0)
+            flush.fill_(1)
+            return cuda_time(fn)
+
+        run(lambda: sw.swept_advance(plan, u, 2 * plan.h + 1))            # warm-up
+        t = min(run(lambda: sw.swept_advance(plan, u, nsteps)) for _ in range(3))
+        launches = sw.swept_plan_last_advance(plan)[:2]
+        rec = {"N": n, "swept": n * nsteps / t, "launches": launches[0], "ring_launches": launches[1]}
+        if name == "uneven":
+            got = u.clone()
+            u.copy_(u0)
+            sw.swept_naive_advance(plan, u, nsteps)
+            rec["bit_exact_vs_naive"] = bool(torch.equal(got, u))
+            rec["wide_windows"] = -(-(n % B) // 32)                 # ceil((N mod B) / 32r), r = 1
+        plan.destroy()
+        out[name] = rec
+    return {"workload": "heat1d_N16777440_r0.25_5000steps_f32c_B512", "unit": UNIT,
+            "even": out["even"], "uneven": out["uneven"],
+            "uneven_over_even": out["uneven"]["swept"] / out["even"]["swept"]}
 
 
 def report_latency_c0(peaks, flush):
@@ -1316,7 +1353,7 @@ def main():
                     help="one GPU: the other workloads' reports after the headline (all), or the "
                          "headline line alone (none; e.g. for a launch list of the headline steps)")
     ap.add_argument("--workload", default="heat",
-                    choices=["heat", "ks", "batch", "adjoint", "latency", "heat_f64", "ks_rk2", "euler"],
+                    choices=["heat", "ks", "batch", "adjoint", "latency", "heat_f64", "ks_rk2", "euler", "uneven"],
                     help="heat: the headline line (with every report on one GPU); the others print one "
                          "line for that workload")
     args = ap.parse_args()
@@ -1326,7 +1363,8 @@ def main():
         return run_batch_workload(args)
     reports = {"ks": ("ks_c2", report_ks_c2), "adjoint": ("adjoint_c4", report_adjoint_c4),
                "latency": ("latency_c0", report_latency_c0), "heat_f64": ("heat_c1_f64", report_heat_f64),
-               "ks_rk2": ("ks_rk2_f1", report_ks_rk2_f1), "euler": ("euler_f2", report_euler_f2)}
+               "ks_rk2": ("ks_rk2_f1", report_ks_rk2_f1), "euler": ("euler_f2", report_euler_f2),
+               "uneven": ("uneven_f4", report_uneven_f4)}
     if args.workload in reports:
         return _report_line(*reports[args.workload], args)
     return run_gpu(args)
