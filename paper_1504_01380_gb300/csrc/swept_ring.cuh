@@ -465,15 +465,30 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
   if (w1 > w0) RingImpl<ST, DT, K>::run(a, sm, w0, w1);
 }
 
+// Warps per block of the streamed kernel: for the widest tiles (K = 32) every
+// warp an SM holds in one block, when the shared memory allows two blocks of
+// four warps or more (registers then cap the kernel as before); else blocks of
+// four warps.  Measured on GB300 (KS, compensated FP32, N = 2^22, B = 1024,
+// 1216 warps, two blocks of four per SM): one block of eight warps per SM
+// 1.44e12 cell-updates/s against 1.34e12, bit for bit the same; heat (three
+// blocks of four, or one of twelve) within 0.3%.  Neither the kernel's
+// registers nor the placement of the blocks on the SMs (pinned to two per SM
+// by padding their shared memory) made the difference.
+template <class DT, int K> struct StreamWarps {
+  static constexpr int value = (K == 32 && RingBlocks<DT, K>::value >= 2) ? 4 * RingBlocks<DT, K>::value
+                                                                          : kWarpsPerBlock;
+};
+
 // Several full-diamond stages in one launch (RingImpl::run_stream); a kernel
 // of its own so that the one-stage kernel keeps its register budget.
 template <int ST, class DT, int K>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, RingBlocks<DT, K>::value)
+__global__ void __launch_bounds__(32 * StreamWarps<DT, K>::value,
+                                  StreamWarps<DT, K>::value == kWarpsPerBlock ? RingBlocks<DT, K>::value : 1)
 swept_stream_kernel(const StageArgs a, int nwarps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
   E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * 32 * K);
-  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (gw >= nwarps) return;
   RingImpl<ST, DT, K>::run_stream(a, sm, gw, nwarps);
 }
@@ -549,11 +564,22 @@ cudaError_t launch_ring_k(const StageArgs& a, int nwarps, cudaStream_t s) {
       const int n = (nw + nwarps - 1) / nwarps;
       return (n <= 16 || per_sm >= per_sm_ring) ? cudaSuccess : cudaErrorNotSupported;
     }
-    const int grid = (nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    // one block per SM where the kernel allows it and every SM holds the same number of warps
+    int wpb = kWarpsPerBlock;
+    if (StreamWarps<DT, K>::value > kWarpsPerBlock && nwarps % sms == 0 && nwarps / sms > kWarpsPerBlock &&
+        nwarps / sms <= StreamWarps<DT, K>::value)
+      wpb = nwarps / sms;
+    const size_t smem_b = smem / kWarpsPerBlock * wpb;
+    if (wpb != kWarpsPerBlock) {
+      e = cudaFuncSetAttribute(swept_stream_kernel<ST, DT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_b);
+      if (e != cudaSuccess) return e;
+    }
+    const int grid = (nwarps + wpb - 1) / wpb;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kWarpsPerBlock * 32);
-    cfg.dynamicSmemBytes = smem;
+    cfg.blockDim = dim3(wpb * 32);
+    cfg.dynamicSmemBytes = smem_b;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
