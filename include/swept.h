@@ -197,10 +197,10 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        neither SWEPT_OPT_PERSISTENT nor SWEPT_OPT_DROP_WINDOW,
  *                        runs in one launch of one thread block cluster (at most
  *                        16 blocks of 4, 2 or 1 warps, one warp per window) when
- *                        the GPU can hold it: each block keeps its windows' stage
- *                        edges in shared memory, the V-fills read their
- *                        neighbours' edges through distributed shared memory,
- *                        and a cluster barrier separates the stages (the latency
+ *                        the GPU can hold it: at the end of a stage each window
+ *                        pushes its edges into the shared memory of the windows
+ *                        that read them (distributed shared memory), and a
+ *                        cluster barrier separates the stages (the latency
  *                        regime of Section 4, without a kernel launch or a
  *                        global-memory round trip per stage).  0: the per-stage
  *                        launches.
@@ -208,7 +208,7 @@ int swept_plan_info(swept_plan_t plan, int64_t *info, int ninfo);
  *                        KS plan runs every step in one thread block cluster
  *                        when N splits into at most 16 parts of 4r to 4094
  *                        points (each block steps its part in shared memory
- *                        with r halo points from its neighbours, one cluster
+ *                        with r halo points its neighbours push to it, one cluster
  *                        barrier per step: the per-step counterpart of
  *                        SWEPT_OPT_RESIDENT); 0 (default): one launch per step.
  *   SWEPT_OPT_DROP_WINDOW failure injection: in the persistent advance window
