@@ -465,18 +465,20 @@ swept_ring_kernel(const StageArgs a, int nwarps) {
   if (w1 > w0) RingImpl<ST, DT, K>::run(a, sm, w0, w1);
 }
 
-// Warps per block of the streamed kernel: for the widest tiles (K = 32) every
-// warp an SM holds in one block, when the shared memory allows two blocks of
-// four warps or more (registers then cap the kernel as before); else blocks of
-// four warps.  Measured on GB300 (KS, compensated FP32, N = 2^22, B = 1024,
-// 1216 warps, two blocks of four per SM): one block of eight warps per SM
-// 1.44e12 cell-updates/s against 1.34e12, bit for bit the same; heat (three
-// blocks of four, or one of twelve) within 0.3%.  Neither the kernel's
+// Warps per block of the streamed kernel: every warp an SM holds in one block
+// where the shared memory bounds the SM at two to four blocks of four warps
+// (the register budget the launch bounds give is then the same as with blocks
+// of four); else blocks of four warps.  Measured on GB300: KS, compensated
+// FP32, N = 2^22, B = 1024, 1216 warps, two blocks of four per SM: one block
+// of eight warps per SM 1.44e12 cell-updates/s against 1.34e12, bit for bit
+// the same; the Euler equations, compensated, N = 2^23, B = 128, four blocks
+// of four: one block of sixteen 2.72e10 cell-steps/s against 2.61e10; heat
+// (three blocks of four, or one of twelve) within 0.3%.  Neither the kernel's
 // registers nor the placement of the blocks on the SMs (pinned to two per SM
 // by padding their shared memory) made the difference.
 template <class DT, int K> struct StreamWarps {
-  static constexpr int value = (K == 32 && RingBlocks<DT, K>::value >= 2) ? 4 * RingBlocks<DT, K>::value
-                                                                          : kWarpsPerBlock;
+  static constexpr int value =
+      RingBlocks<DT, K>::value >= 2 ? kWarpsPerBlock * RingBlocks<DT, K>::value : kWarpsPerBlock;
 };
 
 // Several full-diamond stages in one launch (RingImpl::run_stream); a kernel
