@@ -205,13 +205,14 @@ __device__ bool stream_uneven_wide(const StageArgs& a, typename DT::E* sm, int n
 }
 
 template <int ST, class DT, int K, int KW>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, RingBlocks<DT, KW>::value)
+__global__ void __launch_bounds__(32 * StreamWarps<DT, KW>::value,
+                                  StreamWarps<DT, KW>::value == kWarpsPerBlock ? RingBlocks<DT, KW>::value : 1)
 swept_stream_wide_kernel(const StageArgs a, int nwarps, int nreg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using E = typename DT::E;
   constexpr int BW = 32 * KW;
   E* sm = reinterpret_cast<E*>(smem_raw) + (threadIdx.x >> 5) * (2 * BW);
-  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   bool ok = true;
   if (gw < nwarps) ok = stream_uneven_ring<ST, DT, K>(a, sm, gw, nwarps, nreg);
   else if (nreg + (gw - nwarps) < a.nwin) ok = stream_uneven_wide<ST, DT, K, KW>(a, sm, nreg, gw - nwarps);
@@ -255,11 +256,23 @@ cudaError_t launch_wk(const StageArgs& a, int nreg, int odd, cudaStream_t s, int
     if (nwarps < 1) return cudaErrorInvalidValue;
     if (nwarps + nwide > resident) nwarps = resident - nwide;  // one warp per wide window
     if (nwarps < 1) return cudaErrorInvalidValue;
-    const int grid = (nwarps + nwide + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    // every warp of an SM in one block where the kernel allows it (as for swept_stream_kernel)
+    const int total = nwarps + nwide;
+    int wpb = kWarpsPerBlock;
+    if (StreamWarps<DT, KW>::value > kWarpsPerBlock && total % sms == 0 && total / sms > kWarpsPerBlock &&
+        total / sms <= StreamWarps<DT, KW>::value)
+      wpb = total / sms;
+    const size_t smem_b = smem / kWarpsPerBlock * wpb;
+    if (wpb != kWarpsPerBlock) {
+      e = cudaFuncSetAttribute(swept_stream_wide_kernel<ST, DT, K, KW>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+      if (e != cudaSuccess) return e;
+    }
+    const int grid = (total + wpb - 1) / wpb;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kWarpsPerBlock * 32);
-    cfg.dynamicSmemBytes = smem;
+    cfg.blockDim = dim3(wpb * 32);
+    cfg.dynamicSmemBytes = smem_b;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
