@@ -552,6 +552,28 @@ int swept_advance_noalloc(int64_t N, int stencil_id, const double *params, int n
 #define SWEPT_PROBE_F64_FMA 3
 int swept_probe_alu(int kind, int64_t iters, double *ops, void *stream);
 
+/*
+ * swept_check_div_sqrt -- the Euler flux's binary32 division and square root
+ * beside CUDA's correctly rounded ones (the paper has no counterpart: this
+ * checks an implementation detail of the Euler kernels of Section 7).  The
+ * compensated Euler kernels divide and take square roots with straight-line
+ * code (an approximate reciprocal or reciprocal square root, one Newton step,
+ * Markstein's fma correction) and accept a result only where an exact test
+ * on its remainder proves it is the correctly rounded one; elsewhere they
+ * recompute with the correctly rounded library operation.  This entry runs
+ * both forms on n pairs (a[i], b[i]) in one kernel on `stream`:
+ *   out[i]       straight-line a[i] / b[i]     out[n + i]    __fdiv_rn(a[i], b[i])
+ *   out[2n + i]  straight-line sqrt(a[i])      out[3n + i]   __fsqrt_rn(a[i])
+ *   ok[i]        1 where the division was proven, 0 where a kernel recomputes it
+ *   ok[n + i]    the same for the square root
+ * a, b (n floats each), out (4n floats) and ok (2n ints) are device memory of
+ * the current device, owned by the caller.  Wherever ok is 1 the two results
+ * must agree bit for bit.
+ * Errors: SWEPT_EINVAL (n < 0, a null pointer, memory or a stream of another
+ * device), SWEPT_ECUDA.
+ */
+int swept_check_div_sqrt(const float *a, const float *b, int64_t n, float *out, int *ok, void *stream);
+
 /* ---- diagnostics ------------------------------------------------------ */
 
 /* Name of a status code (static string). */

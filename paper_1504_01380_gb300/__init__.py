@@ -37,6 +37,7 @@ EXPORTS = (
     "swept_batch_plan", "swept_batch_set", "swept_batch_info", "swept_advance_batch",
     "swept_batch_status", "swept_batch_destroy", "swept_adjoint", "swept_batch_naive_advance",
     "swept_plan_status", "swept_plan_last_advance", "swept_probe_alu", "swept_adjoint_scratch",
+    "swept_check_div_sqrt",
     "swept_stage", "swept_edge_copy",
 )
 
@@ -120,6 +121,8 @@ def load(path: str | None = None):
         L.swept_adjoint_scratch.restype = i32
         L.swept_probe_alu.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), vp]
         L.swept_probe_alu.restype = i32
+        L.swept_check_div_sqrt.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.swept_check_div_sqrt.restype = i32
         L.swept_strerror.argtypes = [i32]
         L.swept_strerror.restype = ctypes.c_char_p
         L.swept_version.argtypes = []
@@ -313,6 +316,24 @@ def swept_probe_alu(kind: int, iters: int, stream=None) -> float:
     _check(load().swept_probe_alu(int(kind), int(iters), ctypes.byref(ops), _stream(stream)),
            "swept_probe_alu")
     return float(ops.value)
+
+
+def swept_check_div_sqrt(a, b, stream=None):
+    """The Euler kernels' straight-line binary32 division and square root beside CUDA's
+    correctly rounded ones on float32 device tensors ``a``, ``b`` (same length n).
+    Returns (out, ok): out[0] the straight-line a / b, out[1] __fdiv_rn(a, b), out[2] the
+    straight-line sqrt(a), out[3] __fsqrt_rn(a); ok[0] / ok[1] are 1 where the division /
+    square root was proven correctly rounded (the kernels recompute the rest)."""
+    import torch
+    n = a.numel()
+    if b.numel() != n or a.dtype != torch.float32 or b.dtype != torch.float32:
+        raise ValueError("a and b must be float32 tensors of one length")
+    out = torch.empty((4, n), dtype=torch.float32, device=a.device)
+    ok = torch.empty((2, n), dtype=torch.int32, device=a.device)
+    _check(load().swept_check_div_sqrt(_dev_ptr(a, 4 * n, "a"), _dev_ptr(b, 4 * n, "b"), int(n),
+                                       _dev_ptr(out, 16 * n, "out"), _dev_ptr(ok, 8 * n, "ok"),
+                                       _stream(stream)), "swept_check_div_sqrt")
+    return out, ok
 
 
 def swept_advance_noalloc(N: int, stencil_id: int, params, dtype: int, B: int, u, nsteps: int,

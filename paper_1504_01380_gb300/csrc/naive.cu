@@ -309,7 +309,9 @@ naive_euler_kernel(const T* __restrict__ arg, const T* __restrict__ base, const 
       aR[c] = sa[c][f + 2];
       sR[c] = ss[c][f + 1];
     }
-    euler_face<T>(aL, sL, aR, sR, g1, F);
+    bool ok = true;
+    euler_face<T, true>(aL, sL, aR, sR, g1, F, ok);   // straight-line division and square root
+    if (!ok) euler_face<T>(aL, sL, aR, sR, g1, F);    // where they could not prove their result
 #pragma unroll
     for (int c = 0; c < 3; ++c) sf[c][f] = F[c];
   }

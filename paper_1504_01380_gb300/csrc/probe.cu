@@ -13,6 +13,7 @@
 // nothing is written), into a small array inside the module: the probe
 // allocates nothing.
 #include "swept.h"
+#include "swept_device.cuh"
 #include "swept_internal.h"
 
 namespace swept {
@@ -72,6 +73,22 @@ cudaError_t launch_probe(int64_t iters, double* ops, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The Euler flux's straight-line binary32 division and square root beside
+// CUDA's correctly rounded ones, element by element (see swept_device.cuh).
+__global__ void div_sqrt_check_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
+                                      float* __restrict__ out, int* __restrict__ ok) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = a[i], y = b[i];
+    bool okd = true, oks = true;
+    out[i] = div_tested(x, rcp_tested(y), okd);
+    out[n + i] = __fdiv_rn(x, y);
+    out[2 * n + i] = sqrt_tested(x, oks);
+    out[3 * n + i] = __fsqrt_rn(x);
+    ok[i] = okd ? 1 : 0;
+    ok[n + i] = oks ? 1 : 0;
+  }
+}
+
 }  // namespace
 }  // namespace swept
 
@@ -90,4 +107,15 @@ extern "C" int swept_probe_alu(int kind, int64_t iters, double* ops, void* strea
   if (e == cudaSuccess) return SWEPT_OK;
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? SWEPT_ENOMEM : SWEPT_ECUDA;
+}
+
+extern "C" int swept_check_div_sqrt(const float* a, const float* b, int64_t n, float* out, int* ok, void* stream) {
+  if (n < 0 || (n > 0 && (!a || !b || !out || !ok))) return SWEPT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!swept::call_on_device(-1, s, {a, b, out, ok})) return SWEPT_EINVAL;
+  if (n == 0) return SWEPT_OK;
+  const int64_t blocks = (n + 255) / 256;
+  swept::div_sqrt_check_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(a, b, n, out, ok);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SWEPT_OK : SWEPT_ECUDA;
 }
