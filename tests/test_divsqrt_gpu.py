@@ -21,8 +21,20 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 B_LO, B_HI = 2.0 ** -30, 2.0 ** 31          # divisor range of the straight-line division
-A_LO, A_HI = 2.0 ** -72, 2.0 ** 91          # numerator range (or a = +-0)
 X_LO, X_HI = 2.0 ** -100, 2.0 ** 101        # square-root range (or x = +-0)
+# quotient range: the binary32 number just below |a / b| has an exponent in [-72, 120]
+Q_BIASED_LO, Q_BIASED_HI = 127 - 72, 127 + 120
+
+
+def _div_in_range(a, b, qref):
+    """Where the straight-line division applies: b in range, and a = +-0 or the exponent
+    of the number just below the correctly rounded |a / b| in range (NaN and infinite
+    quotients are out)."""
+    with np.errstate(invalid="ignore"):
+        inb = (np.abs(b) >= B_LO) & (np.abs(b) < B_HI)
+        t = ((qref.view(np.uint32) - np.uint32(1)) >> np.uint32(23)) & np.uint32(0xff)
+        inq = (t >= Q_BIASED_LO) & (t <= Q_BIASED_HI) & np.isfinite(qref)
+    return inb & ((a == 0) | inq)
 
 
 def _f32(x):
@@ -83,29 +95,31 @@ def test_random_bit_patterns(cuda_lib):
     b = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32).view(np.float32)
     out, ok = _run(cuda_lib, a, b)
     _check_proven_equal(out, ok)
+    ind = _div_in_range(a, b, out[1])
     with np.errstate(invalid="ignore"):
-        inb = (np.abs(b) >= B_LO) & (np.abs(b) < B_HI)
-        ina = (np.abs(a) >= A_LO) & (np.abs(a) < A_HI)
         inx = (a >= X_LO) & (a < X_HI)
-    # outside the range nothing is accepted (a zero numerator is in range)
-    assert not (ok[0] & ~(inb & (ina | (a == 0)))).any()
+    # outside the range nothing is accepted; inside it nearly everything is
+    assert not (ok[0] & ~ind).any()
     assert not (ok[1] & ~inx).any()
-    # inside it nearly everything is
-    assert ok[0][inb & ina].mean() > 0.999
+    assert ind.sum() > n // 8 and ok[0][ind].mean() > 0.999
     assert ok[1][inx].mean() > 0.999
 
 
 def test_operands_across_the_range(cuda_lib):
     rng = np.random.default_rng(7)
     n = 1 << 19
-    a = _log_uniform(rng, A_LO, A_HI, n)
+    a = _log_uniform(rng, 2.0 ** -100, 2.0 ** 127, n)
     b = _log_uniform(rng, B_LO, B_HI, n)
     k = min(a.size, b.size)
     a, b = a[:k], b[:k]
     out, ok = _run(cuda_lib, a, b)
     _check_proven_equal(out, ok)
-    assert ok[0].mean() > 0.9999
+    ind = _div_in_range(a, b, out[1])
+    assert not (ok[0] & ~ind).any()
+    assert ind.mean() > 0.5 and ok[0][ind].mean() > 0.9999
     x = np.abs(a)
+    x = x[(x >= X_LO) & (x < X_HI)]
+    b = b[: x.size]
     out, ok = _run(cuda_lib, x, b)
     _check_proven_equal(out, ok)
     assert ok[1].mean() > 0.9999
@@ -149,19 +163,29 @@ def test_exact_results_powers_of_two_and_zeros(cuda_lib):
 
 def test_range_edges_and_specials(cuda_lib):
     f = np.float32
+    up = lambda v: np.nextafter(f(v), f(np.inf))
     dn = lambda v: np.nextafter(f(v), f(-np.inf))
+    # divisors: the edges of their range, with a quotient well inside
     b_in = [B_LO, dn(B_HI), -B_LO, -dn(B_HI), 1.0]
     b_out = [dn(B_LO), B_HI, -B_HI, 1e-40, np.inf, -np.inf, np.nan, 0.0, -0.0]
-    a_in = [A_LO, dn(A_HI), -A_LO, 0.75]
-    a_out = [dn(A_LO), A_HI, 1e-42, np.inf, np.nan]
-    a = np.array([x for x in a_in for _ in b_in] + [x for x in a_out for _ in b_in]
-                 + [0.75 for _ in b_out], dtype=np.float32)
-    b = np.array(b_in * len(a_in) + b_in * len(a_out) + b_out, dtype=np.float32)
+    # quotients at the edges of theirs, from exact products with powers of two
+    q_in = [up(2.0 ** -72), f(3 * 2.0 ** -73), 2.0 ** 100, dn(2.0 ** 121), -up(2.0 ** -72)]
+    q_out = [2.0 ** -72, dn(2.0 ** -72), 2.0 ** -100, up(2.0 ** 121), -(2.0 ** -72)]
+    scale = [1.0, -1.0, 2.0 ** -6, 2.0 ** 6]
+    a, b, want = [], [], []
+    for bb in b_in:
+        a.append(0.75 * bb); b.append(bb); want.append(True)
+    for bb in b_out:
+        a.append(0.75); b.append(bb); want.append(False)
+    for q, w in [(q, True) for q in q_in] + [(q, False) for q in q_out]:
+        for c in scale:
+            a.append(float(q) * c); b.append(c); want.append(w)
+    for x in (1e-42, np.inf, -np.inf, np.nan):       # subnormal, infinite and NaN numerators
+        a.append(x); b.append(1.0); want.append(False)
+    a, b, want = np.array(a, dtype=np.float32), np.array(b, dtype=np.float32), np.array(want)
     out, ok = _run(cuda_lib, a, b)
     _check_proven_equal(out, ok)
-    n_in = len(a_in) * len(b_in)
-    assert ok[0][:n_in].all()
-    assert not ok[0][n_in:].any()
+    assert np.array_equal(ok[0], want), np.flatnonzero(ok[0] != want)
     x = np.array([X_LO, dn(X_HI), 1.0, dn(X_LO), X_HI, -1.0, -X_LO, 1e-42, np.inf, np.nan], dtype=np.float32)
     out, ok = _run(cuda_lib, x, np.ones_like(x))
     _check_proven_equal(out, ok)
