@@ -7,8 +7,8 @@
 // GB300 that barrier (with a remote shared-memory load) takes about 0.27 us,
 // where a stage boundary through global memory and a kernel launch costs
 // about 2.4 us (the latency tau of Eq. 1 on this GPU), and every window still
-// has a warp of its own (one per warp scheduler), as with the per-stage
-// launches.  Nothing waits on a flag: the barrier is the only synchronisation.
+// has a warp of its own (at most one per warp scheduler), as with the
+// per-stage launches.  Nothing waits on a flag: the barrier is the only synchronisation.
 #include <cooperative_groups.h>
 #include <type_traits>
 
@@ -23,10 +23,14 @@ namespace swept {
 
 namespace {
 
-// Warps per block W (4, 2 or 1: the largest that divides nwin) and blocks C
-// = nwin / W of a plan's cluster; false when C would exceed 16.
+// Warps per block W (1, 2 or 4: the smallest that divides nwin and keeps
+// C <= 16) and blocks C = nwin / W of a plan's cluster; false when none
+// does.  Spreading the windows over more SMs measured faster for FP64 (an
+// SM's warp schedulers share its FP64 pipe; heat, N = 1024: 337 -> 318 ns
+// per sub-timestep at 32 windows on 16 SMs instead of 8, 582 -> 527 at 16
+// windows) and the same for the compensated state.
 bool cluster_shape(int nwin, int& W, int& C) {
-  for (W = 4; W >= 1; W /= 2) {
+  for (W = 1; W <= 4; W *= 2) {
     if (nwin % W == 0 && nwin / W <= 16) {
       C = nwin / W;
       return true;
