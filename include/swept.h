@@ -120,7 +120,10 @@ typedef struct swept_plan_s *swept_plan_t;
  *           integrator; 1 Euler equations).
  *   B       tile width: 32*K points with K in {1,2,4,8,16,32}, K % radius
  *           == 0 (Section 3 gives each node an even count of points; in
- *           general B % (2*radius) == 0).  B = 0 picks the tuned default.
+ *           general B % (2*radius) == 0).  B = 0 picks the measured
+ *           default: the widest tile that divides N or tiles it unevenly, up
+ *           to 1024 points from N = 2^22 on and 512 below (Euler equations:
+ *           64 in FP64, 128 compensated).
  *   params  host pointer; copied.
  * Allocates the edge double-buffer (2 * 2N values, 32N bytes; 64N for the
  * Runge-Kutta pairs; 288N / 192N for FP64 / F32C Euler point states) on

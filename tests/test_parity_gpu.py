@@ -310,3 +310,17 @@ def test_plain_launches_same_bits(cuda_lib, stencil, dtype):
     want = oracle_run(stencil, dtype, u0, nsteps)
     assert_same(plan, run_gpu(sw, plan, u0, nsteps), want)
     assert_same(plan, run_gpu(sw, plan, u0, nsteps, naive=True), want)
+
+
+@pytest.mark.parametrize("stencil,N,want_B", [(HEAT, 1 << 22, 1024), (KS, 1 << 22, 1024), (HEAT, 1 << 21, 512),
+                                              (KS, (1 << 22) + 64, 1024)])
+def test_default_tile_width(cuda_lib, stencil, N, want_B):
+    """B = 0: 1024-point tiles from N = 2^22 on (uneven tiling included), 512 below; the
+    advance with the default tile equals the naive stepper bit for bit (3h + 5 steps)."""
+    sw = cuda_lib
+    r = 1 if stencil == HEAT else 2
+    plan = sw.swept_plan(N, r, stencil, params_of(stencil), F32C, 0)
+    assert plan.B == want_B
+    u0 = initial(stencil, N, 77)
+    nsteps = 3 * plan.h + 5
+    assert_same(plan, run_gpu(sw, plan, u0, nsteps), run_gpu(sw, plan, u0, nsteps, naive=True))
